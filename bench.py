@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark: forward + backward of one view of a 3.0M-splat scene at 1256x828.
+
+A step is one pass of the whole path over one view: projection, depth sort,
+binning, forward blending, summed L1 loss, backward blending with per-splat
+reduction, and the chain rule to the 3D parameters.  Inputs are resident in
+HBM; the scene's parameters (708 MB) are larger than L2.  One JSON line on
+stdout (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W]         the CUDA path
+  python bench.py --impl reference [...]                  the FP64 CPU oracle
+
+Under torchrun each rank renders its own view of the same scene (orbit angle
+2 pi rank / N): views are independent, so no data-path collective (weak
+scaling); ranks only meet at barriers and for the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/view, splat-frags/s at 3M/1256x828, FP16 vs FP32 state; p99 latency"
+WORKLOAD = "mipnerf360-shaped synthetic scene, 3.0M splats SH3, 1256x828, L1 loss, fwd+bwd"
+N_SPLATS = 3_000_000
+STAGES = ("project", "sort", "bin", "blend_fwd", "loss", "blend_bwd", "project_bwd")
+KERNELS_PER_STAGE = {"project": 1, "sort": 4, "bin": None, "blend_fwd": 1, "loss": 1,
+                     "blend_bwd": 1, "project_bwd": 1}   # bin: 2 + pair-sort passes
+# Nominal FP32 rate (SM count x FP32 lanes x 2 flop x max SM clock): raster stages are
+# plain FP32 ALU work, for which the measured peaks carry no figure.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FLOP_PER_FRAG_FWD = 20.0
+FLOP_PER_FRAG_BWD = 70.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=N_SPLATS, help="splat count (smaller for profiling)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="main timed loop only (no fp16 run, e2e, CPU baseline, clocks)")
+    ap.add_argument("--cpu-pixels", type=int, default=48, help="pixels in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2505_18764_gb300 as gs
+    from paper_2505_18764_gb300 import _lib
+    import synthetic as syn
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.time()
+    scene_np, cam0, target_np = syn.mipnerf_scene_3m(args.n)
+    cam = syn.orbit_camera(2.0 * math.pi * rank / world, 4.0, 50.0, cam0.width, cam0.height)
+    log(f"[rank {rank}] scene generated in {time.time() - t0:.1f}s")
+    scene = gs.SceneTensors.from_numpy(scene_np, dev)
+    target = torch.from_numpy(target_np).to(dev)
+    H, W = cam.height, cam.width
+    opts = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4)
+    ws = gs.Workspace(scene.n, W, H, opts, device=dev)
+    ccam = gs.camera_to_c(cam)
+    stream = torch.cuda.current_stream(dev)
+    image = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    last = torch.empty((H, W), dtype=torch.int32, device=dev)
+    dl = torch.empty_like(image)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    grads = gs.zero_grads(scene)
+
+    def make_step(ws, o, state):
+        def step(events=None):
+            def mark(i):
+                if events is not None:
+                    events[i].record(stream)
+            mark(0)
+            gs.project(ws, scene, ccam, o, stream)
+            mark(1)
+            gs.sort(ws, stream)
+            mark(2)
+            gs.bin(ws, ccam, o, stream)
+            mark(3)
+            gs.blend_forward(ws, ccam, o, image, state, last, None, stream)
+            mark(4)
+            gs.loss(image, target, "l1", dl, loss, stream)
+            mark(5)
+            gs.blend_backward(ws, ccam, o, state, last, dl, stream)
+            mark(6)
+            gs.project_backward(ws, scene, ccam, o, grads, stream)
+            mark(7)
+        return step
+
+    def timed(step, K, W_):
+        for _ in range(W_):
+            step()
+        torch.cuda.synchronize(dev)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter()
+        for k in range(K):
+            step(ev[k])
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        total = ev[0][0].elapsed_time(ev[-1][7])
+        per = {s: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
+               for i, s in enumerate(STAGES)}
+        step_ms = [ev[k][0].elapsed_time(ev[k][7]) for k in range(K)]
+        return total, per, step_ms, t_wall
+
+    state32 = gs.alloc_state(H, W, "fp32", dev)
+    step32 = make_step(ws, opts, state32)
+    clocks = ClockSampler(local_rank)
+    # warm-up, then the timed region for the headline number
+    for _ in range(args.warmup):
+        step32()
+    torch.cuda.synchronize(dev)
+    if not args.no_extras:
+        clocks.start()
+    total_ms, per_stage, step_ms, t_wall = timed(step32, args.steps, 0)
+    clk = clocks.stop() if not args.no_extras else None
+    gs.check_status(ws, stream)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    ms_per_view = total_ms_max / (args.steps * world)
+
+    # counters of this view (untimed): visible splats, pairs, fragments
+    out = gs.render(ws, scene, ccam, opts, stream, want_n_contrib=True)
+    cnt = gs.read_counters(ws, stream)
+    F = int(out["n_contrib"].sum().item())
+    n_front = int(((scene.means @ torch.as_tensor(cam.viewmat[2, :3], device=dev)) +
+                   float(cam.viewmat[2, 3]) > 0.2).sum().item())
+    V, P = cnt["visible"], cnt["pairs"]
+    npix = H * W
+    passes = ws.c.pair_passes
+    kernels_per_step = 1 + 4 + (2 + passes) + 1 + 1 + 1 + 1
+    K_sh = 16
+
+    # algorithmic bytes (HBM-bound stages) and flops (raster stages) per launch
+    alg = {
+        "project": ("hbm", scene.n * 20 + n_front * 28 + V * (12 * K_sh + 48)),
+        "sort": ("hbm", scene.n * 4 + 56 * V),
+        "bin": ("hbm", 148 * V + (8 + 16 * passes + 4) * P),
+        "blend_fwd": ("alu", FLOP_PER_FRAG_FWD * F),
+        "loss": ("hbm", 36 * npix),
+        "blend_bwd": ("alu", FLOP_PER_FRAG_BWD * F),
+        "project_bwd": ("hbm", V * (48 + 236 + 2 * 236)),
+    }
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    stage_roof = {}
+    for s, (bound, amount) in alg.items():
+        ms = per_stage[s]
+        if bound == "hbm":
+            ach = amount / (ms * 1e-3) / 1e9
+            stage_roof[s] = dict(bound="hbm", achieved=round(ach, 1), unit="GB/s",
+                                 frac=round(ach / hbm_peak, 4), ms=round(ms, 4))
+        else:
+            ach = amount / (ms * 1e-3) / 1e12
+            stage_roof[s] = dict(bound="alu", achieved=round(ach, 3), unit="TFLOP/s",
+                                 frac=round(ach / FP32_PEAK_TFLOPS, 4), ms=round(ms, 4))
+    dom = max(per_stage, key=per_stage.get)
+    dr = stage_roof[dom]
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        if tj.get("kernel_stage") == dom and tj.get("source_hash") == _source_hash():
+            traffic = tj.get("bytes_per_launch")
+    roofline = dict(kernel=dom, bound=dr["bound"], achieved=dr["achieved"],
+                    peak=round(hbm_peak, 1) if dr["bound"] == "hbm" else round(FP32_PEAK_TFLOPS, 2),
+                    unit=dr["unit"], frac=dr["frac"], traffic=traffic,
+                    peak_source="MEASURED_PEAKS.json hbm_gbs (measured)" if dr["bound"] == "hbm"
+                    else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)")
+
+    res = dict(metric=METRIC, value=round(ms_per_view, 4), unit="ms/view", n_gpus=world,
+               steps=args.steps, warmup=args.warmup, ms_per_step=round(total_ms_max / args.steps, 4),
+               higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32",
+               data="synthetic",
+               config=dict(workload=WORKLOAD, splats=scene.n, width=W, height=H, sh_degree=3,
+                           state_format="fp32", t_cull=1e-4, reduce="block", loss="l1",
+                           views_per_step=world, parallelism=f"replicas x{world}",
+                           l2="inputs larger than L2 (scene parameters 708 MB > 129 MB)"),
+               counts=dict(visible=V, pairs=P, fragments=F, in_front=n_front, pixels=npix),
+               splat_frags_per_s=round(F / (ms_per_view * 1e-3), 1),
+               stages_ms=per_stage, stage_roofline=stage_roof,
+               p50_ms=round(float(np.percentile(step_ms, 50)), 4),
+               p99_ms=round(float(np.percentile(step_ms, 99)), 4),
+               wall_ms_per_step=round(t_wall * 1e3 / args.steps, 4),
+               gpu_launches=kernels_per_step * args.steps * world,
+               roofline=roofline)
+
+    if not args.no_extras:
+        # FP16 saved state, same work otherwise
+        o16 = gs.RasterOpts(state_format="fp16", sh_degree=3, t_cull=1e-4)
+        ws16 = gs.Workspace(scene.n, W, H, o16, device=dev)
+        st16 = gs.alloc_state(H, W, "fp16", dev)
+        tot16, per16, _, _ = timed(make_step(ws16, o16, st16), args.steps, args.warmup)
+        res["fp16_state"] = dict(ms_per_view=round(tot16 / args.steps, 4),
+                                 speedup_vs_fp32=round((total_ms / args.steps) / (tot16 / args.steps), 4),
+                                 stages_ms=per16)
+        del ws16
+        res["e2e"] = run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, state32,
+                             last, dl, loss, grads, ws)
+        res["clocks"] = clk
+        if world == 1:
+            res["cpu_baseline"] = cpu_baseline(args, scene_np, cam, target_np)
+    return res
+
+
+def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, state, last, dl, loss,
+            grads, ws):
+    """Same step through the C ABI with host buffers: every step copies the scene
+    parameters and the target from pinned host memory and reads the gradients
+    and the loss back."""
+    host_in = [t.cpu().pin_memory() for t in scene.tensors()] + [target.cpu().pin_memory()]
+    dev_in = list(scene.tensors()) + [target]
+    gnames = ("means", "scales", "quats", "opacities", "sh")
+    host_out = [grads[k].cpu().pin_memory() for k in gnames] + [loss.cpu().pin_memory()]
+    dev_out = [grads[k] for k in gnames] + [loss]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def step():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        for g in gnames:
+            grads[g].zero_()
+        gs.project(ws, scene, ccam, opts, stream)
+        gs.sort(ws, stream)
+        gs.raster_forward(ws, ccam, opts, image, state, last, None, stream=stream)
+        gs.loss(image, target, "l1", dl, loss, stream)
+        gs.raster_backward(ws, scene, ccam, opts, state, last, dl, grads, stream)
+        for h, d in zip(host_out, dev_out):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    K = max(1, min(args.steps, 20))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return dict(value=round(a.elapsed_time(b) / K, 4), unit="ms/view", h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=d2h, steps=K)
+
+
+def _source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2505_18764_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+def oracle_sample(scene_np, cam, target_np, n_pixels, seed):
+    """One bounded sample of the view: full preprocessing (projection + depth
+    order of every splat) and forward + backward of n_pixels random pixels,
+    extrapolated to the whole image."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(cam.width * cam.height, size=n_pixels, replace=False).astype(np.int32)
+    g = np.sign(rng.uniform(-1, 1, size=(cam.height, cam.width, 3)))  # L1 loss gradient stand-in
+    t0 = time.perf_counter()
+    out = oracle.backward(scene_np, cam, g, oracle.opts_array(t_cull=1e-4), pixels=pix, timings=True)
+    wall = time.perf_counter() - t0
+    tm = out["timings"]
+    est_s = tm["preprocess_s"] + tm["trace_s"] * (cam.width * cam.height) / n_pixels
+    return est_s, wall, tm
+
+
+def cpu_baseline(args, scene_np, cam, target_np):
+    import oracle
+    est_s, wall, tm = oracle_sample(scene_np, cam, target_np, args.cpu_pixels, seed=123)
+    return dict(value=round(est_s * 1e3, 1), unit="ms/view", cores=oracle.num_threads(),
+                kind="oracle",
+                sample=(f"FP64 oracle: projection + depth order of all {scene_np.n} splats "
+                        f"({tm['preprocess_s']:.2f}s) and fwd+bwd of {args.cpu_pixels} random pixels "
+                        f"({tm['trace_s']:.2f}s), trace time scaled by {cam.width * cam.height}/"
+                        f"{args.cpu_pixels} pixels; wall {wall:.1f}s"))
+
+
+def run_reference(args, rank, world):
+    import oracle
+    import synthetic as syn
+    if rank != 0:
+        return None
+    scene_np, cam, target_np = syn.mipnerf_scene_3m(args.n)
+    oracle.build()
+    for w in range(args.warmup):
+        oracle_sample(scene_np, cam, target_np, 8, seed=w)
+    ests, walls = [], []
+    for k in range(args.steps):
+        est_s, wall, _ = oracle_sample(scene_np, cam, target_np, args.cpu_pixels, seed=1000 + k)
+        ests.append(est_s)
+        walls.append(wall)
+    v = float(np.mean(ests)) * 1e3
+    return dict(metric=METRIC, value=round(v, 1), unit="ms/view", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=round(v, 1), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, splats=scene_np.n, width=cam.width,
+                            height=cam.height, sh_degree=3, state_format="fp64 (no rounding)",
+                            t_cull=1e-4, loss="l1"),
+                cpu_baseline=dict(value=round(v, 1), unit="ms/view", cores=oracle.num_threads(),
+                                  kind="oracle",
+                                  sample=f"per step: all-splat preprocessing + fwd+bwd of "
+                                         f"{args.cpu_pixels} random pixels, scaled to the full view"),
+                e2e=dict(value=round(v, 1), unit="ms/view", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0),
+                wall_s_per_step=round(float(np.mean(walls)), 2))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,270 @@
+/*
+ * gsr.h -- C ABI of the GB300 differentiable Gaussian-splat rasterizer.
+ *
+ * The library renders depth-sorted 3D Gaussian splats and back-propagates
+ * per-pixel image gradients to per-splat parameter gradients, following
+ * "Efficient Differentiable Hardware Rasterization for 3D Gaussian Splatting"
+ * (arXiv 2505.18764).  Pipeline per view:
+ *
+ *   gs_project          per-splat EWA projection, SH colour, culling, depth key
+ *                       (Sec. 2.1.1 Eq. 1, Sec. 2.1.2)
+ *   gs_sort             global stable depth sort (Onesweep radix sort, Sec. 4.1)
+ *   gs_raster_forward   quad-coverage binning + front-to-back alpha blending
+ *                       with the 1/255 floor and T-culling (Eq. 2, Sec. 2.1.4)
+ *   gs_raster_backward  front-to-back gradient recurrence (Eq. 5-7, Procedure 1),
+ *                       per-splat reduction (Sec. 3.2, Procedure 2) and the chain
+ *                       rule back to the 3D parameters
+ *   gs_render_batch     a list of forward / forward+backward requests
+ *
+ * Conventions
+ *   - Every array pointer is CUDA device memory owned by the caller, row-major,
+ *     float32 unless stated.  Host pointers are marked "host".
+ *   - Calls are asynchronous on `stream` (a cudaStream_t) and never allocate:
+ *     scratch lives in a caller-allocated workspace (gs_workspace_size /
+ *     gs_workspace_init).  One workspace serves one stream at a time.
+ *   - Parameters are activated values: scales > 0, opacities in [0, 1],
+ *     quaternions (w, x, y, z) normalised inside, SH coefficients [N][K][3]
+ *     with K = (sh_degree + 1)^2, real orthonormal basis with the
+ *     Condon-Shortley phase, index l*l + l + m.
+ *   - Return value: GS_OK or a negative GS_ERR_*; gs_last_error() gives a
+ *     message (per calling thread).  Conditions found on the device (pair
+ *     capacity exceeded, a bounded wait that gave up) are recorded in the
+ *     workspace's status word and reported by gs_check_status.
+ */
+#ifndef GSR_H_
+#define GSR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st* gs_stream_t;
+
+enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = -1, /* bad pointer, size, or a size beyond the workspace's capacity */
+  GS_ERR_CAPACITY = -2,    /* more (splat, block) pairs than the workspace holds */
+  GS_ERR_TIMEOUT = -3,     /* a device-side bounded wait (sort / scan look-back) gave up */
+  GS_ERR_CUDA = -4         /* a CUDA runtime call failed */
+};
+
+/* Saved per-pixel state format (Sec. 3.3): colour C (3) and transmittance T. */
+enum {
+  GS_STATE_FP32 = 0,    /* float4  (r, g, b, T), 16 B / pixel */
+  GS_STATE_FP16 = 1,    /* half4   (r, g, b, T),  8 B / pixel */
+  GS_STATE_UNORM16 = 2, /* ushort4 (r, g, b, T),  8 B / pixel, colours saturated to [0, 1] */
+  GS_STATE_UNORM8 = 3   /* uchar4  (r, g, b, T),  4 B / pixel, colours saturated to [0, 1] */
+};
+
+/* Per-splat gradient reduction in the backward raster (Sec. 3.2). */
+enum {
+  GS_REDUCE_BLOCK = 0, /* warp transpose-reduce + cross-warp sum: one atomic per (splat, 16x16 block) */
+  GS_REDUCE_WARP = 1,  /* warp reduce: one atomic per (splat, warp) */
+  GS_REDUCE_NAIVE = 2  /* one atomic per fragment (the paper's 1x baseline) */
+};
+
+enum { GS_MODE_FORWARD = 0, GS_MODE_FORWARD_BACKWARD = 1 };
+enum { GS_LOSS_NONE = 0, GS_LOSS_L1 = 1, GS_LOSS_L2 = 2 };
+
+/* Pinhole camera.  viewmat: row-major 3x4 world->camera [R | t], OpenCV axes
+ * (x right, y down, z forward).  Pixel (x, y) has its centre at (x+0.5, y+0.5);
+ * mu_2D = (fx tx/tz + cx, fy ty/tz + cy).  Splats with tz <= znear are culled. */
+typedef struct gs_camera {
+  float viewmat[12];
+  float campos[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float znear;
+} gs_camera;
+
+typedef struct gs_raster_opts {
+  int32_t state_format;     /* GS_STATE_* */
+  int32_t reduce_mode;      /* GS_REDUCE_* */
+  int32_t reduce_threshold; /* X of Sec. 3.2.3: warps with fewer active lanes add directly */
+  int32_t sh_degree;        /* 0..3 */
+  float t_cull;             /* skip fragment i iff T_i < t_cull (Procedure 1); 0 disables */
+  int32_t reserved;
+  int64_t pair_capacity;    /* (splat, 16x16 block) pairs the workspace holds; 0 = 16 per splat */
+} gs_raster_opts;
+
+/* Host-side descriptor of a caller-allocated device workspace.  Filled by
+ * gs_workspace_init; gs_project binds it to a scene size and camera. */
+typedef struct gs_workspace {
+  void* base;      /* device memory, >= gs_workspace_size bytes, 256-B aligned */
+  size_t bytes;
+  int32_t n_cap, width_cap, height_cap, reserved;
+  int64_t pair_cap;
+  /* bound by gs_project (read by the later calls) */
+  int32_t n, width, height, sh_degree;
+  int32_t state_format, clamp01, pair_passes, sorted_in_b;
+  uint64_t layout[24]; /* byte offsets of the internal arrays */
+} gs_workspace;
+
+/* Scene and request for gs_render_batch. */
+typedef struct gs_scene_ref {
+  const float* means;     /* [n][3] */
+  const float* scales;    /* [n][3] */
+  const float* quats;     /* [n][4] */
+  const float* opacities; /* [n]    */
+  const float* sh;        /* [n][K][3] */
+  int32_t n;
+  int32_t sh_degree;
+} gs_scene_ref;
+
+typedef struct gs_request {
+  gs_scene_ref scene;
+  gs_camera camera;
+  gs_raster_opts opts;
+  int32_t mode;          /* GS_MODE_* */
+  int32_t loss_kind;     /* GS_LOSS_*: with NONE, dL_dimage is an input */
+  float* image;          /* [H][W][3] out, may be null */
+  void* state;           /* [H][W] pixels of the state format, out */
+  uint32_t* last;        /* [H][W] depth rank of the last fragment, 0xFFFFFFFF if none */
+  uint32_t* n_contrib;   /* [H][W] fragment count, may be null */
+  const float* target;   /* [H][W][3], used with L1 / L2 */
+  float* dL_dimage;      /* [H][W][3]: written by L1 / L2, read otherwise */
+  double* loss;          /* one double, written by L1 / L2 (summed over pixels and channels) */
+  float* d_means;        /* gradients, accumulated (+=) */
+  float* d_scales;
+  float* d_quats;
+  float* d_opacities;
+  float* d_sh;
+} gs_request;
+
+/* Bytes of device workspace for scenes of up to n_cap splats and images of up
+ * to width_cap x height_cap pixels.  opts->pair_capacity sets the (splat,
+ * block) pair capacity.  Host pointers in, host size out. */
+int gs_workspace_size(int32_t n_cap, int32_t width_cap, int32_t height_cap,
+                      const gs_raster_opts* opts, size_t* bytes);
+
+/* Lays the workspace out in `device_base` (caller-owned, >= bytes).  `ws` is a
+ * host struct the caller owns; nothing is allocated. */
+int gs_workspace_init(gs_workspace* ws, void* device_base, size_t bytes, int32_t n_cap,
+                      int32_t width_cap, int32_t height_cap, const gs_raster_opts* opts);
+
+/* Per-splat projection (Sec. 2.1.2): t = W mu + w, cull if tz <= znear,
+ * Sigma_2D = J W R S S^T R^T W^T J^T + 0.3 I, conic = Sigma_2D^-1,
+ * colour = max(0, sum_k sh_k Y_k(normalize(mu - campos)) + 0.5) (and <= 1 for
+ * the unorm formats, Sec. 3.3), opacity floor o >= 1/255, and the screen-space
+ * bounding box of the alpha >= 1/255 ellipse (the quad of Sec. 1).  Writes
+ * the projected records, depth keys and the visible count into `ws`. */
+int gs_project(gs_workspace* ws, const float* means, const float* scales, const float* quats,
+               const float* opacities, const float* sh, int32_t n, const gs_camera* cam,
+               const gs_raster_opts* opts, gs_stream_t stream);
+
+/* Stable ascending sort of the visible splats by camera depth (FP32 bits of
+ * tz), ties by splat index; the count is read on the device (Sec. 4.1). */
+int gs_sort(gs_workspace* ws, gs_stream_t stream);
+
+/* Bins every visible splat into the 16x16 pixel blocks its quad covers (in
+ * depth order), then blends front to back per pixel (Eq. 2): alpha =
+ * min(0.99, o exp(power)), fragments with alpha < 1/255 or T_i < t_cull
+ * skipped.  Outputs: image [H][W][3] (may be null), state [H][W] in
+ * opts->state_format, last [H][W] (depth rank of the last fragment, or
+ * 0xFFFFFFFF), n_contrib [H][W] (may be null). */
+int gs_raster_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                      float* image, void* state, uint32_t* last, uint32_t* n_contrib,
+                      gs_stream_t stream);
+
+/* The two halves of gs_raster_forward, callable separately (e.g. to time the
+ * rasterization apart from binning, as the paper's Table "tab:perf" splits
+ * "rasterization" from "overall"):
+ *   gs_bin           (splat, block) pairs of every visible splat's quad, sorted
+ *                    by block with depth order kept inside each block, and the
+ *                    per-block ranges (the quad rasterization step, Sec. 1);
+ *   gs_blend_forward front-to-back blending of each block's list (Eq. 2).
+ * Same arguments and outputs as gs_raster_forward. */
+int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, gs_stream_t stream);
+int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                     float* image, void* state, uint32_t* last, uint32_t* n_contrib,
+                     gs_stream_t stream);
+
+/* Backward pass.  Re-traverses the forward's lists front to back with
+ * (C'_1, T_1) = (stored C, 1) and the recurrences of Eq. 5 and Eq. 6, takes
+ * dL/dc_i and dL/dalpha_i from Eq. 3 and Eq. 7 (Procedure 1), reduces them per
+ * splat (opts->reduce_mode, Sec. 3.2) and applies the chain rule to the 3D
+ * parameters.  Gradients are ADDED to d_* (callers zero them), so several views
+ * can accumulate.  Must follow gs_raster_forward on the same workspace, scene,
+ * camera and opts.  dL_dimage [H][W][3]. */
+int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales,
+                       const float* quats, const float* opacities, const float* sh, int32_t n,
+                       const gs_camera* cam, const gs_raster_opts* opts, const void* state,
+                       const uint32_t* last, const float* dL_dimage, float* d_means,
+                       float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                       gs_stream_t stream);
+
+/* The two halves of gs_raster_backward:
+ *   gs_blend_backward   per-pixel gradients of Procedure 1 (Eq. 3, 5-7) reduced
+ *                       per splat (Sec. 3.2) into the workspace's per-splat
+ *                       2D accumulators (mu_2D, conic, colour, opacity);
+ *   gs_project_backward chain rule from those to the 3D parameters (added to
+ *                       d_*).  Same arguments as gs_raster_backward. */
+int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                      const void* state, const uint32_t* last, const float* dL_dimage,
+                      gs_stream_t stream);
+int gs_project_backward(gs_workspace* ws, const float* means, const float* scales,
+                        const float* quats, const float* opacities, const float* sh, int32_t n,
+                        const gs_camera* cam, const gs_raster_opts* opts, float* d_means,
+                        float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                        gs_stream_t stream);
+
+/* Summed image loss over n_values floats: L1 = sum |image - target| (dL/dimage =
+ * sign) or L2 = sum (image - target)^2 (dL/dimage = 2 (image - target)).
+ * Writes dL_dimage (may be null) and *loss (one device double). */
+int gs_loss(const float* image, const float* target, int64_t n_values, int32_t kind,
+            float* dL_dimage, double* loss, gs_stream_t stream);
+
+/* Runs the requests in order on one stream with one workspace (sized for the
+ * largest).  Forward: project, sort, raster.  Forward+backward adds the loss
+ * (if any) and the backward pass. */
+int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stream_t stream);
+
+/* Synchronises `stream` and returns the device status recorded in `ws`
+ * (GS_OK, GS_ERR_CAPACITY or GS_ERR_TIMEOUT). */
+int gs_check_status(gs_workspace* ws, gs_stream_t stream);
+
+/* Message of the calling thread's last error ("" if none).  Host string. */
+const char* gs_last_error(void);
+
+/* Introspection for tests and metrics.  gs_read_counters synchronises `stream`
+ * and writes (host) out[0] = visible splats V, out[1] = pairs P, out[2] =
+ * device status, out[3] = 16x16 blocks of the bound camera. */
+int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
+
+/* Copies an internal array of `ws` into caller device memory `dst` (`bytes`):
+ * GS_ARRAY_SORTED_IDS u32 [V], GS_ARRAY_DEPTH_KEYS u32 [n] (0xFFFFFFFF = culled),
+ * GS_ARRAY_RECORDS float [n][12] (mu_x, mu_y, A, B, C, thr, o, ext_x, r, g, b,
+ * ext_y with (A, B, C) = -log2(e) (a/2, b, c/2) of the conic and thr =
+ * log2(1/(255 o))), GS_ARRAY_PAIR_BLOCKS u32 [P], GS_ARRAY_PAIR_RANKS u32 [P]
+ * (sorted by block), GS_ARRAY_RANGES u32 [blocks][2], GS_ARRAY_GRAD2D float
+ * [V][12] (per depth rank: the backward's unscaled accumulators). */
+enum {
+  GS_ARRAY_SORTED_IDS = 0,
+  GS_ARRAY_DEPTH_KEYS = 1,
+  GS_ARRAY_RECORDS = 2,
+  GS_ARRAY_PAIR_BLOCKS = 3,
+  GS_ARRAY_PAIR_RANKS = 4,
+  GS_ARRAY_RANGES = 5,
+  GS_ARRAY_GRAD2D = 6
+};
+int gs_copy_array(gs_workspace* ws, int32_t which, void* dst, size_t bytes, gs_stream_t stream);
+
+/* Stable LSD radix sort of n (u32 key, u32 value) pairs on key bits
+ * [0, key_bits), using the workspace's depth-sort buffers (n <= ws->n_cap).
+ * keys_in/vals_in are read; the result goes to keys_out/vals_out (device,
+ * caller-owned, n entries; must not alias the inputs).  keys must be below
+ * 2^key_bits rounded up to whole bytes.  Uses the workspace's scratch and header, so it
+ * invalidates a view bound by gs_project.  Standalone use of the sort of Sec. 4.1. */
+int gs_sort_pairs(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* vals_in,
+                  uint32_t* keys_out, uint32_t* vals_out, int32_t n, int32_t key_bits,
+                  gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H_ */

@@ -144,10 +144,12 @@ def render(scene, cam, opts=None, pixels=None):
     return out
 
 
-def backward(scene, cam, dLdC, opts=None, quant_cprime: bool = False):
+def backward(scene, cam, dLdC, opts=None, quant_cprime: bool = False, pixels=None,
+             timings: bool = False):
     """Analytic backward for dL/dC [H, W, 3].  Returns dict of gradients
     (means, scales, quats, opacities, sh), the per-splat 2D gradients g2d [N, 9]
-    (mu2 x/y, conic a/b/c, rgb, opacity) and the image."""
+    (mu2 x/y, conic a/b/c, rgb, opacity) and the image.  With `pixels`, only
+    those pixels (linear index y*W+x) are traced and contribute."""
     opts = opts_array() if opts is None else opts
     keep, args = _scene_args(scene)
     camv = camera_array(cam)
@@ -157,11 +159,17 @@ def backward(scene, cam, dLdC, opts=None, quant_cprime: bool = False):
     gm, gs, gq, go = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros((N, 4)), np.zeros(N)
     gsh = np.zeros((N, K, 3))
     g2d = np.zeros((N, 9))
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
+    tm = np.zeros(2)
     rc = _load().oracle_backward(*args, _ptr(camv), _ptr(opts), _ptr(g), ctypes.c_int(int(quant_cprime)),
+                                 _ptr(pix), ctypes.c_int(0 if pix is None else pix.shape[0]),
                                  _ptr(image), _ptr(gm), _ptr(gs), _ptr(gq), _ptr(go), _ptr(gsh),
-                                 _ptr(g2d))
+                                 _ptr(g2d), _ptr(tm))
     assert rc == 0
-    return dict(means=gm, scales=gs, quats=gq, opacities=go, sh=gsh, g2d=g2d, image=image)
+    out = dict(means=gm, scales=gs, quats=gq, opacities=go, sh=gsh, g2d=g2d, image=image)
+    if timings:
+        out["timings"] = dict(preprocess_s=float(tm[0]), trace_s=float(tm[1]))
+    return out
 
 
 def splat_grads(scene, cam, dLdC, ids, opts=None):

@@ -32,6 +32,7 @@
 // code are available).  Every function below is pinned by tests (closed forms,
 // invariants, library special functions, finite differences, brute force).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -181,18 +182,37 @@ double poly_eval(const std::vector<double>& c, double z) {
   return r;
 }
 
+// Per (l, |m|): normalisation and the coefficients of d^m P_l / dz^m and of
+// d^(m+1) P_l / dz^(m+1), built once from the formulas above.
+struct ShTables {
+  double K[4][4];
+  std::vector<double> q[4][4], q1[4][4];
+  ShTables() {
+    for (int l = 0; l <= 3; ++l)
+      for (int am = 0; am <= l; ++am) {
+        K[l][am] = std::sqrt((2.0 * l + 1.0) / (4.0 * kPi) * factorial(l - am) / factorial(l + am));
+        q[l][am] = legendre_deriv_coeffs(l, am);
+        q1[l][am] = legendre_deriv_coeffs(l, am + 1);
+      }
+  }
+};
+
+const ShTables& sh_tables() {
+  static const ShTables t;  // thread-safe initialisation
+  return t;
+}
+
 // Evaluates all (deg+1)^2 basis functions at a unit direction; optional gradient.
 void sh_basis(int deg, const double dir[3], double* Y, double* dY /* [K][3] or null */) {
+  const ShTables& tab = sh_tables();
   const double x = dir[0], y = dir[1], z = dir[2];
   for (int l = 0; l <= deg; ++l) {
     for (int m = -l; m <= l; ++m) {
       const int am = std::abs(m);
-      const double K = std::sqrt((2.0 * l + 1.0) / (4.0 * kPi) * factorial(l - am) / factorial(l + am));
+      const double K = tab.K[l][am];
       const double cs = (am % 2) ? -1.0 : 1.0;  // (-1)^m Condon-Shortley phase
-      std::vector<double> q = legendre_deriv_coeffs(l, am);
-      std::vector<double> q1 = legendre_deriv_coeffs(l, am + 1);
-      const double Q = poly_eval(q, z);
-      const double Qz = poly_eval(q1, z);
+      const double Q = poly_eval(tab.q[l][am], z);
+      const double Qz = poly_eval(tab.q1[l][am], z);
       // w^m and w^(m-1) with w = x + i y
       double re = 1.0, im = 0.0, re1 = 0.0, im1 = 0.0;
       for (int k = 0; k < am; ++k) {
@@ -665,30 +685,37 @@ int oracle_render(int N, const double* means, const double* scales, const double
   return 0;
 }
 
-// Full backward: dL/dC [H][W][3] -> parameter gradients (overwritten, not
+// Backward: dL/dC [H][W][3] -> parameter gradients (overwritten, not
 // accumulated).  Optionally returns the image and the per-splat 2D gradients.
 // quant_cprime: if nonzero, C'_1 is the stored colour rounded with opts.quant
 // (emulates a reduced-precision saved state read back by the backward pass).
+// pixels (linear y*W+x) restricts the traced pixels to a subset (null = all);
+// the image is then written for the listed pixels only.  timings (if non-null)
+// receives the seconds spent in projection + depth order and in tracing.
 int oracle_backward(int N, const double* means, const double* scales, const double* quats,
                     const double* opac, const double* sh, int deg, const double* camv,
-                    const double* optv, const double* dLdC, int quant_cprime, double* image,
-                    double* g_means, double* g_scales, double* g_quats, double* g_opac,
-                    double* g_sh, double* g2d_out) {
+                    const double* optv, const double* dLdC, int quant_cprime, const int32_t* pixels,
+                    int npix, double* image, double* g_means, double* g_scales, double* g_quats,
+                    double* g_opac, double* g_sh, double* g2d_out, double* timings) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
   const Camera cam = read_camera(camv);
   const Opts op = read_opts(optv);
   Scene sc{N, means, scales, quats, opac, sh, deg};
   std::vector<Splat> sp;
   project_all(sc, cam, op.clamp01, sp);
   const std::vector<int> ord = depth_order(sp);
+  const auto t1 = clk::now();
   const int nt = num_threads();
   std::vector<double> acc(static_cast<size_t>(nt) * N * kG2, 0.0);
-  const int npx = cam.W * cam.H;
+  const int total = pixels ? npix : cam.W * cam.H;
 #pragma omp parallel
   {
     std::vector<Frag> fr;
     double* mine = acc.data() + static_cast<size_t>(thread_id()) * N * kG2;
 #pragma omp for schedule(dynamic, 8)
-    for (int p = 0; p < npx; ++p) {
+    for (int q = 0; q < total; ++q) {
+      const int p = pixels ? pixels[q] : q;
       PixelResult r;
       trace_pixel(p % cam.W, p / cam.W, sp, ord, cam, op, &fr, r);
       if (image) for (int c = 0; c < 3; ++c) image[static_cast<size_t>(p) * 3 + c] = r.C[c];
@@ -711,6 +738,11 @@ int oracle_backward(int N, const double* means, const double* scales, const doub
     splat_backward(sp[i], g2.data() + static_cast<size_t>(i) * kG2, sh + static_cast<size_t>(i) * K * 3,
                    deg, cam, op.clamp01, g_means + 3 * i, g_scales + 3 * i, g_quats + 4 * i,
                    g_opac + i, g_sh + static_cast<size_t>(i) * K * 3);
+  const auto t2 = clk::now();
+  if (timings) {
+    timings[0] = std::chrono::duration<double>(t1 - t0).count();
+    timings[1] = std::chrono::duration<double>(t2 - t1).count();
+  }
   return 0;
 }
 

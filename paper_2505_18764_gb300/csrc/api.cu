@@ -1,0 +1,545 @@
+// C ABI: workspace layout, argument checks and the launch sequence of each call.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace gsr {
+
+// launchers (kernels live in the other translation units)
+struct CamDev;
+cudaError_t launch_project_fwd(const float*, const float*, const float*, const float*, const float*,
+                               int, int, const gs_camera&, int, SplatRec*, uint32_t*, Header*,
+                               uint2*, int, uint32_t*, int, cudaStream_t);
+cudaError_t launch_project_bwd(const float*, const float*, const float*, const float*, const float*,
+                               int, int, const gs_camera&, int, const uint32_t*, const float*,
+                               const Header*, float*, float*, float*, float*, float*, int,
+                               cudaStream_t);
+cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,
+                                 const uint32_t*, uint32_t, uint32_t, uint32_t, int, uint32_t,
+                                 const uint32_t*, unsigned long long*, uint32_t*, const uint32_t*,
+                                 uint32_t, uint32_t*, int, int, cudaStream_t);
+cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
+cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
+cudaError_t launch_bin(const uint32_t*, const SplatRec*, SplatRec*, float*, Header*,
+                       unsigned long long*, const uint32_t*, uint32_t*, uint32_t*, uint32_t, int, int,
+                       int, int, int, int, cudaStream_t);
+cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, cudaStream_t);
+cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const SplatRec*, int, int, int, int,
+                              float, int, float*, void*, uint32_t*, uint32_t*, cudaStream_t);
+cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const SplatRec*, int, int, int, int,
+                              float, int, const void*, const uint32_t*, const float*, float*, int,
+                              int, cudaStream_t);
+cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
+                        cudaStream_t);
+size_t sort_tiles(size_t n);
+size_t bin_tiles(size_t n);
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define GS_CUDA(call, where)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+// Resident CTAs of a 256-thread sort/bin kernel per SM (shared memory bound).
+constexpr int kPersistentPerSm = 6;
+
+enum Slot {
+  L_HDR = 0,
+  L_EPOCH,
+  L_STATUS,      // onesweep look-back words, shared by all passes (tags differ)
+  L_SCAN,        // binning scan look-back words
+  L_KEYS,        // [n] depth keys (0xFFFFFFFF = culled)
+  L_KA, L_VA, L_KB, L_VB,   // [n] sort ping-pong
+  L_REC,         // [n] records by splat id
+  L_REC_SORTED,  // [n] records by depth rank
+  L_G2D,         // [n][12] backward accumulators by depth rank
+  L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
+  L_RANGES,      // [blocks_cap] uint2
+  L_END
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int64_t default_pair_cap(int64_t n_cap) {
+  int64_t p = 16 * n_cap;
+  if (p < (1 << 22)) p = 1 << 22;
+  return p;
+}
+
+int blocks_of(int w, int h, int& gw, int& gh) {
+  gw = (w + kBlock - 1) / kBlock;
+  gh = (h + kBlock - 1) / kBlock;
+  return gw * gh;
+}
+
+bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint64_t* off,
+                    size_t* total) {
+  int gw, gh;
+  const size_t blocks = blocks_of(w_cap, h_cap, gw, gh);
+  const size_t st_tiles = std::max(sort_tiles(n_cap), sort_tiles(pair_cap)) + 1;
+  size_t sz[L_END];
+  sz[L_HDR] = sizeof(Header);
+  sz[L_EPOCH] = 256;
+  sz[L_STATUS] = st_tiles * 256 * sizeof(unsigned long long);
+  sz[L_SCAN] = (bin_tiles(n_cap) + 1) * sizeof(unsigned long long);
+  sz[L_KEYS] = n_cap * 4;
+  sz[L_KA] = sz[L_VA] = sz[L_KB] = sz[L_VB] = n_cap * 4;
+  sz[L_REC] = sz[L_REC_SORTED] = sz[L_G2D] = n_cap * sizeof(SplatRec);
+  sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
+  sz[L_RANGES] = blocks * sizeof(uint2);
+  size_t o = 0;
+  for (int i = 0; i < L_END; ++i) {
+    off[i] = o;
+    o = align256(o + sz[i]);
+  }
+  *total = o;
+  return true;
+}
+
+template <typename T>
+T* at(const gs_workspace* ws, int slot) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws->base) + ws->layout[slot]);
+}
+
+int check_opts(const gs_raster_opts* o) {
+  if (!o) return fail(GS_ERR_INVALID_ARG, "opts is null");
+  if (o->state_format < 0 || o->state_format > 3) return fail(GS_ERR_INVALID_ARG, "bad state_format %d", o->state_format);
+  if (o->reduce_mode < 0 || o->reduce_mode > 2) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
+  if (o->sh_degree < 0 || o->sh_degree > kMaxShDegree) return fail(GS_ERR_INVALID_ARG, "bad sh_degree %d", o->sh_degree);
+  if (!(o->t_cull >= 0.f && o->t_cull <= 1.f)) return fail(GS_ERR_INVALID_ARG, "t_cull must be in [0, 1]");
+  if (o->pair_capacity < 0 || o->pair_capacity >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [0, 2^30)");
+  return GS_OK;
+}
+
+int check_ws(const gs_workspace* ws) {
+  if (!ws || !ws->base) return fail(GS_ERR_INVALID_ARG, "workspace is null or not initialised");
+  return GS_OK;
+}
+
+int check_cam(const gs_workspace* ws, const gs_camera* cam) {
+  if (!cam) return fail(GS_ERR_INVALID_ARG, "camera is null");
+  if (cam->width < 0 || cam->height < 0) return fail(GS_ERR_INVALID_ARG, "negative image size");
+  if (cam->width > ws->width_cap || cam->height > ws->height_cap)
+    return fail(GS_ERR_INVALID_ARG, "image %dx%d exceeds the workspace capacity %dx%d", cam->width,
+                cam->height, ws->width_cap, ws->height_cap);
+  return GS_OK;
+}
+
+int pair_passes_for(int blocks) {
+  int bits = 0;
+  while (bits < 32 && (1ll << bits) < blocks) ++bits;
+  int p = (bits + 7) / 8;
+  return p < 1 ? 1 : p;
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" {
+
+const char* gs_last_error(void) { return g_last_error.c_str(); }
+
+int gs_workspace_size(int32_t n_cap, int32_t width_cap, int32_t height_cap,
+                      const gs_raster_opts* opts, size_t* bytes) {
+  if (!bytes) return fail(GS_ERR_INVALID_ARG, "bytes is null");
+  if (n_cap < 0 || width_cap < 0 || height_cap < 0) return fail(GS_ERR_INVALID_ARG, "negative capacity");
+  if (n_cap >= (1 << 30)) return fail(GS_ERR_INVALID_ARG, "n_cap must be < 2^30");
+  if (width_cap > 65535 * kBlock || height_cap > 65535 * kBlock)
+    return fail(GS_ERR_INVALID_ARG, "image capacity too large");
+  {
+    int gw, gh;
+    if ((int64_t)((width_cap + kBlock - 1) / kBlock) * ((height_cap + kBlock - 1) / kBlock) > (1 << 21))
+      return fail(GS_ERR_INVALID_ARG, "image capacity above 2^21 pixel blocks");
+    (void)gw; (void)gh;
+  }
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  const int64_t pcap = opts->pair_capacity ? opts->pair_capacity : default_pair_cap(n_cap);
+  if (pcap >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair capacity must be < 2^30");
+  uint64_t off[L_END];
+  compute_layout(n_cap, width_cap, height_cap, pcap, off, bytes);
+  return GS_OK;
+}
+
+int gs_workspace_init(gs_workspace* ws, void* device_base, size_t bytes, int32_t n_cap,
+                      int32_t width_cap, int32_t height_cap, const gs_raster_opts* opts) {
+  if (!ws) return fail(GS_ERR_INVALID_ARG, "ws is null");
+  size_t need = 0;
+  int rc = gs_workspace_size(n_cap, width_cap, height_cap, opts, &need);
+  if (rc) return rc;
+  if (!device_base) return fail(GS_ERR_INVALID_ARG, "device_base is null");
+  if (reinterpret_cast<uintptr_t>(device_base) & 255)
+    return fail(GS_ERR_INVALID_ARG, "device_base must be 256-byte aligned");
+  if (bytes < need) return fail(GS_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", bytes, need);
+  std::memset(ws, 0, sizeof(*ws));
+  ws->base = device_base;
+  ws->bytes = bytes;
+  ws->n_cap = n_cap;
+  ws->width_cap = width_cap;
+  ws->height_cap = height_cap;
+  ws->pair_cap = opts->pair_capacity ? opts->pair_capacity : default_pair_cap(n_cap);
+  static_assert(L_END <= 24, "layout table too small");
+  size_t total = 0;
+  compute_layout(n_cap, width_cap, height_cap, ws->pair_cap, ws->layout, &total);
+  // Header, epoch and all look-back words start at zero (a zero word never
+  // carries a valid tag's flag).  Synchronous: runs once per workspace.
+  GS_CUDA(cudaMemset(device_base, 0, ws->layout[L_SCAN + 1]), "workspace init memset");
+  GS_CUDA(cudaDeviceSynchronize(), "workspace init sync");
+  return GS_OK;
+}
+
+int gs_project(gs_workspace* ws, const float* means, const float* scales, const float* quats,
+               const float* opacities, const float* sh, int32_t n, const gs_camera* cam,
+               const gs_raster_opts* opts, gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (!rc) rc = check_opts(opts);
+  if (!rc) rc = check_cam(ws, cam);
+  if (rc) return rc;
+  if (n < 0 || n > ws->n_cap) return fail(GS_ERR_INVALID_ARG, "n = %d exceeds the workspace capacity %d", n, ws->n_cap);
+  if (n > 0 && (!means || !scales || !quats || !opacities || !sh))
+    return fail(GS_ERR_INVALID_ARG, "null scene pointer");
+  if (reinterpret_cast<uintptr_t>(quats) & 15) return fail(GS_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int gw, gh;
+  const int blocks = blocks_of(cam->width, cam->height, gw, gh);
+  ws->n = n;
+  ws->width = cam->width;
+  ws->height = cam->height;
+  ws->sh_degree = opts->sh_degree;
+  ws->state_format = opts->state_format;
+  ws->clamp01 = opts->state_format == GS_STATE_UNORM16 || opts->state_format == GS_STATE_UNORM8;
+  ws->pair_passes = pair_passes_for(blocks);
+  GS_CUDA(cudaMemsetAsync(at<Header>(ws, L_HDR), 0, sizeof(Header), st), "gs_project memset");
+  GS_CUDA(launch_project_fwd(means, scales, quats, opacities, sh, n, opts->sh_degree, *cam,
+                             ws->clamp01, at<SplatRec>(ws, L_REC), at<uint32_t>(ws, L_KEYS),
+                             at<Header>(ws, L_HDR), at<uint2>(ws, L_RANGES), blocks,
+                             at<uint32_t>(ws, L_EPOCH), num_sms(), st),
+          "project kernel");
+  return GS_OK;
+}
+
+int gs_sort(gs_workspace* ws, gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Header* hdr = at<Header>(ws, L_HDR);
+  const uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
+  unsigned long long* status = at<unsigned long long>(ws, L_STATUS);
+  const int grid_cap = num_sms() * kPersistentPerSm;
+  uint32_t* bufs_k[2] = {at<uint32_t>(ws, L_KA), at<uint32_t>(ws, L_KB)};
+  uint32_t* bufs_v[2] = {at<uint32_t>(ws, L_VA), at<uint32_t>(ws, L_VB)};
+  for (int pass = 0; pass < 4; ++pass) {
+    const uint32_t* kin = pass == 0 ? at<uint32_t>(ws, L_KEYS) : bufs_k[(pass + 1) & 1];
+    const uint32_t* vin = pass == 0 ? nullptr : bufs_v[(pass + 1) & 1];
+    uint32_t* kout = bufs_k[pass & 1];
+    uint32_t* vout = bufs_v[pass & 1];
+    GS_CUDA(launch_onesweep_pass(kin, vin, kout, vout, pass == 0 ? nullptr : &hdr->visible,
+                                 (uint32_t)ws->n, (uint32_t)ws->n, (uint32_t)ws->n, 8 * pass, 0xFFu,
+                                 hdr->depth_hist[pass], status, &hdr->tile_counter[pass], epoch,
+                                 (uint32_t)pass, &hdr->status, pass == 0, grid_cap, st),
+            "depth sort pass");
+  }
+  ws->sorted_in_b = 1;  // four passes: a, b, a, b
+  return GS_OK;
+}
+
+static int check_bound(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts) {
+  int rc = check_ws(ws);
+  if (!rc) rc = check_opts(opts);
+  if (!rc) rc = check_cam(ws, cam);
+  if (rc) return rc;
+  if (cam->width != ws->width || cam->height != ws->height)
+    return fail(GS_ERR_INVALID_ARG, "camera differs from the one gs_project was given");
+  if (opts->state_format != ws->state_format || opts->sh_degree != ws->sh_degree)
+    return fail(GS_ERR_INVALID_ARG, "opts differ from the ones gs_project was given");
+  return GS_OK;
+}
+
+int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Header* hdr = at<Header>(ws, L_HDR);
+  const uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
+  int gw, gh;
+  blocks_of(cam->width, cam->height, gw, gh);
+  const int grid_cap = num_sms() * kPersistentPerSm;
+  GS_CUDA(launch_bin(at<uint32_t>(ws, L_VB), at<SplatRec>(ws, L_REC), at<SplatRec>(ws, L_REC_SORTED),
+                     at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN), epoch,
+                     at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PVA), (uint32_t)ws->pair_cap,
+                     cam->width, cam->height, gw, ws->pair_passes, ws->n, grid_cap, st),
+          "bin kernel");
+  uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
+  uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};
+  for (int q = 0; q < ws->pair_passes; ++q) {
+    GS_CUDA(launch_onesweep_pass(pk[q & 1], pv[q & 1], pk[(q + 1) & 1], pv[(q + 1) & 1],
+                                 &hdr->pairs, 0u, (uint32_t)ws->pair_cap, (uint32_t)ws->pair_cap,
+                                 8 * q, 0xFFu, hdr->pair_hist[q], at<unsigned long long>(ws, L_STATUS),
+                                 &hdr->tile_counter[4 + q], epoch, 4u + q, &hdr->status, 0,
+                                 grid_cap, st),
+            "pair sort pass");
+  }
+  const int fin = ws->pair_passes & 1;
+  GS_CUDA(launch_ranges(pk[fin], hdr, at<uint2>(ws, L_RANGES), num_sms(), st), "ranges kernel");
+  return GS_OK;
+}
+
+int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                     float* image, void* state, uint32_t* last, uint32_t* n_contrib,
+                     gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
+  int gw, gh;
+  blocks_of(cam->width, cam->height, gw, gh);
+  const int fin = ws->pair_passes & 1;
+  GS_CUDA(launch_raster_fwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+                            at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
+                            opts->t_cull, opts->state_format, image, state, last, n_contrib,
+                            reinterpret_cast<cudaStream_t>(stream)),
+          "raster forward kernel");
+  return GS_OK;
+}
+
+int gs_raster_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                      float* image, void* state, uint32_t* last, uint32_t* n_contrib,
+                      gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
+  rc = gs_bin(ws, cam, opts, stream);
+  if (rc) return rc;
+  return gs_blend_forward(ws, cam, opts, image, state, last, n_contrib, stream);
+}
+
+int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                      const void* state, const uint32_t* last, const float* dL_dimage,
+                      gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last || !dL_dimage))
+    return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
+  int gw, gh;
+  blocks_of(cam->width, cam->height, gw, gh);
+  const int fin = ws->pair_passes & 1;
+  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+                            at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
+                            opts->t_cull, opts->state_format, state, last, dL_dimage,
+                            at<float>(ws, L_G2D), opts->reduce_mode, opts->reduce_threshold,
+                            reinterpret_cast<cudaStream_t>(stream)),
+          "raster backward kernel");
+  return GS_OK;
+}
+
+int gs_project_backward(gs_workspace* ws, const float* means, const float* scales,
+                        const float* quats, const float* opacities, const float* sh, int32_t n,
+                        const gs_camera* cam, const gs_raster_opts* opts, float* d_means,
+                        float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                        gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
+  if (n > 0 && (!means || !scales || !quats || !opacities || !sh || !d_means || !d_scales ||
+                !d_quats || !d_opacities || !d_sh))
+    return fail(GS_ERR_INVALID_ARG, "null parameter or gradient pointer");
+  GS_CUDA(launch_project_bwd(means, scales, quats, opacities, sh, ws->n, ws->sh_degree, *cam,
+                             ws->clamp01, at<uint32_t>(ws, L_VB), at<float>(ws, L_G2D),
+                             at<Header>(ws, L_HDR), d_means, d_scales, d_quats, d_opacities, d_sh,
+                             num_sms(), reinterpret_cast<cudaStream_t>(stream)),
+          "projection backward kernel");
+  return GS_OK;
+}
+
+int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales,
+                       const float* quats, const float* opacities, const float* sh, int32_t n,
+                       const gs_camera* cam, const gs_raster_opts* opts, const void* state,
+                       const uint32_t* last, const float* dL_dimage, float* d_means,
+                       float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                       gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
+  if (n > 0 && (!means || !scales || !quats || !opacities || !sh || !d_means || !d_scales ||
+                !d_quats || !d_opacities || !d_sh))
+    return fail(GS_ERR_INVALID_ARG, "null parameter or gradient pointer");
+  rc = gs_blend_backward(ws, cam, opts, state, last, dL_dimage, stream);
+  if (rc) return rc;
+  return gs_project_backward(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
+                             d_scales, d_quats, d_opacities, d_sh, stream);
+}
+
+int gs_loss(const float* image, const float* target, int64_t n_values, int32_t kind,
+            float* dL_dimage, double* loss, gs_stream_t stream) {
+  if (kind != GS_LOSS_L1 && kind != GS_LOSS_L2) return fail(GS_ERR_INVALID_ARG, "bad loss kind %d", kind);
+  if (n_values < 0) return fail(GS_ERR_INVALID_ARG, "negative n_values");
+  if (!loss || (n_values > 0 && (!image || !target)))
+    return fail(GS_ERR_INVALID_ARG, "null pointer");
+  GS_CUDA(launch_loss(image, target, n_values, kind, dL_dimage, loss, num_sms(),
+                      reinterpret_cast<cudaStream_t>(stream)),
+          "loss kernel");
+  return GS_OK;
+}
+
+int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stream_t stream) {
+  if (n < 0 || (n > 0 && !reqs)) return fail(GS_ERR_INVALID_ARG, "bad request list");
+  for (int i = 0; i < n; ++i) {
+    const gs_request& q = reqs[i];
+    if (q.opts.sh_degree != q.scene.sh_degree)
+      return fail(GS_ERR_INVALID_ARG, "request %d: opts.sh_degree differs from the scene's", i);
+    int rc = gs_project(ws, q.scene.means, q.scene.scales, q.scene.quats, q.scene.opacities,
+                        q.scene.sh, q.scene.n, &q.camera, &q.opts, stream);
+    if (!rc) rc = gs_sort(ws, stream);
+    if (!rc) rc = gs_raster_forward(ws, &q.camera, &q.opts, q.image, q.state, q.last, q.n_contrib, stream);
+    if (!rc && q.mode == GS_MODE_FORWARD_BACKWARD) {
+      const int64_t nv = (int64_t)q.camera.width * q.camera.height * 3;
+      if (q.loss_kind != GS_LOSS_NONE) {
+        if (!q.image) return fail(GS_ERR_INVALID_ARG, "request %d: a loss needs the image", i);
+        rc = gs_loss(q.image, q.target, nv, q.loss_kind, q.dL_dimage, q.loss, stream);
+      }
+      if (!rc)
+        rc = gs_raster_backward(ws, q.scene.means, q.scene.scales, q.scene.quats, q.scene.opacities,
+                                q.scene.sh, q.scene.n, &q.camera, &q.opts, q.state, q.last,
+                                q.dL_dimage, q.d_means, q.d_scales, q.d_quats, q.d_opacities,
+                                q.d_sh, stream);
+    } else if (!rc && q.mode != GS_MODE_FORWARD) {
+      return fail(GS_ERR_INVALID_ARG, "request %d: bad mode %d", i, q.mode);
+    }
+    if (rc) return rc;
+  }
+  return GS_OK;
+}
+
+int gs_check_status(gs_workspace* ws, gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t status = 0;
+  GS_CUDA(cudaMemcpyAsync(&status, &at<Header>(ws, L_HDR)->status, 4, cudaMemcpyDeviceToHost, st),
+          "status copy");
+  GS_CUDA(cudaStreamSynchronize(st), "status sync");
+  if (status & kStatusTimeout) return fail(GS_ERR_TIMEOUT, "a device-side look-back wait gave up");
+  if (status & kStatusCapacity) {
+    uint32_t want = 0;
+    cudaMemcpy(&want, &at<Header>(ws, L_HDR)->pairs_wanted, 4, cudaMemcpyDeviceToHost);
+    return fail(GS_ERR_CAPACITY, "%u (splat, block) pairs needed, capacity %lld", want,
+                (long long)ws->pair_cap);
+  }
+  return GS_OK;
+}
+
+int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  if (!out) return fail(GS_ERR_INVALID_ARG, "out is null");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t h[4] = {0, 0, 0, 0};
+  GS_CUDA(cudaMemcpyAsync(h, at<Header>(ws, L_HDR), 16, cudaMemcpyDeviceToHost, st), "counter copy");
+  GS_CUDA(cudaStreamSynchronize(st), "counter sync");
+  int gw, gh;
+  out[0] = h[1];
+  out[1] = h[2];
+  out[2] = h[0];
+  out[3] = blocks_of(ws->width, ws->height, gw, gh);
+  return GS_OK;
+}
+
+int gs_copy_array(gs_workspace* ws, int32_t which, void* dst, size_t bytes, gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  if (!dst && bytes) return fail(GS_ERR_INVALID_ARG, "dst is null");
+  const int fin = ws->pair_passes & 1;
+  int slot;
+  size_t cap;
+  int gw, gh;
+  switch (which) {
+    case GS_ARRAY_SORTED_IDS: slot = L_VB; cap = (size_t)ws->n_cap * 4; break;
+    case GS_ARRAY_DEPTH_KEYS: slot = L_KEYS; cap = (size_t)ws->n_cap * 4; break;
+    case GS_ARRAY_RECORDS: slot = L_REC; cap = (size_t)ws->n_cap * sizeof(SplatRec); break;
+    case GS_ARRAY_PAIR_BLOCKS: slot = fin ? L_PKB : L_PKA; cap = (size_t)ws->pair_cap * 4; break;
+    case GS_ARRAY_PAIR_RANKS: slot = fin ? L_PVB : L_PVA; cap = (size_t)ws->pair_cap * 4; break;
+    case GS_ARRAY_RANGES: slot = L_RANGES; cap = (size_t)blocks_of(ws->width_cap, ws->height_cap, gw, gh) * 8; break;
+    case GS_ARRAY_GRAD2D: slot = L_G2D; cap = (size_t)ws->n_cap * 48; break;
+    default: return fail(GS_ERR_INVALID_ARG, "unknown array %d", which);
+  }
+  if (bytes > cap) return fail(GS_ERR_INVALID_ARG, "asked for %zu bytes, array holds %zu", bytes, cap);
+  GS_CUDA(cudaMemcpyAsync(dst, at<char>(ws, slot), bytes, cudaMemcpyDeviceToDevice,
+                          reinterpret_cast<cudaStream_t>(stream)),
+          "array copy");
+  return GS_OK;
+}
+
+int gs_sort_pairs(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* vals_in,
+                  uint32_t* keys_out, uint32_t* vals_out, int32_t n, int32_t key_bits,
+                  gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  if (n < 0 || n > ws->n_cap) return fail(GS_ERR_INVALID_ARG, "n = %d exceeds the capacity %d", n, ws->n_cap);
+  if (key_bits < 1 || key_bits > 32) return fail(GS_ERR_INVALID_ARG, "key_bits must be in [1, 32]");
+  if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return fail(GS_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Header* hdr = at<Header>(ws, L_HDR);
+  uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
+  const int passes = (key_bits + 7) / 8;
+  GS_CUDA(cudaMemsetAsync(hdr, 0, sizeof(Header), st), "sort memset");
+  GS_CUDA(launch_bump_epoch(epoch, st), "epoch kernel");
+  GS_CUDA(launch_digit_hist(keys_in, (uint32_t)n, passes, &hdr->depth_hist[0][0], num_sms(), st), "histogram kernel");
+  uint32_t* bk[2] = {at<uint32_t>(ws, L_KA), at<uint32_t>(ws, L_KB)};
+  uint32_t* bv[2] = {at<uint32_t>(ws, L_VA), at<uint32_t>(ws, L_VB)};
+  const int grid_cap = num_sms() * kPersistentPerSm;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t* kin = p == 0 ? keys_in : bk[(p + 1) & 1];
+    const uint32_t* vin = p == 0 ? vals_in : bv[(p + 1) & 1];
+    uint32_t* kout = p == passes - 1 ? keys_out : bk[p & 1];
+    uint32_t* vout = p == passes - 1 ? vals_out : bv[p & 1];
+    const uint32_t mask = 0xFFu;
+    GS_CUDA(launch_onesweep_pass(kin, vin, kout, vout, nullptr, (uint32_t)n, (uint32_t)n, (uint32_t)n,
+                                 8 * p, mask, hdr->depth_hist[p], at<unsigned long long>(ws, L_STATUS),
+                                 &hdr->tile_counter[9 + p], epoch, 8u + p, &hdr->status, 0,
+                                 grid_cap, st),
+            "sort pass");
+  }
+  return GS_OK;
+}
+
+}  // extern "C"

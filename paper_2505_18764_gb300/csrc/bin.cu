@@ -1,0 +1,220 @@
+// Quad coverage -> (16x16 block, depth rank) pairs, in depth order.
+//
+// The paper rasterizes each depth-sorted splat as a screen quad bounding its
+// alpha >= 1/255 ellipse (Sec. 1, Sec. 2.2) into fixed O(N) buffers.  Here the
+// quad's pixel-centre box is turned into the list of 16x16 pixel blocks it
+// touches.  One fused kernel, one tile of 1024 depth ranks per CTA:
+//   1. gathers each splat's record into depth order (the raster reads
+//      records by rank) and zeroes its backward accumulators,
+//   2. counts its blocks and scans the counts across tiles with a decoupled
+//      look-back (tagged 64-bit status words, bounded waits),
+//   3. writes the pairs with all 256 threads sharing the tile's pairs
+//      (a binary search in the tile's scan finds each pair's splat), so one
+//      very large splat does not serialise on one thread,
+//   4. accumulates the 8-bit digit histograms of the block ids that the
+//      stable pair sort by block needs (depth order survives within a block).
+// Pairs beyond the capacity are not written; the shortfall is recorded.
+#include "common.cuh"
+
+namespace gsr {
+
+constexpr int kBinThreads = 256;
+constexpr int kBinItems = 4;
+constexpr int kBinTile = kBinThreads * kBinItems;  // 1024 ranks
+constexpr unsigned long long kBinAgg = 1ull << 30;
+constexpr unsigned long long kBinPre = 2ull << 30;
+constexpr unsigned long long kBinCount = (1ull << 30) - 1;
+
+// Pixel-centre box of a record, clamped to the image, in block units.
+__device__ __forceinline__ bool record_blocks(const SplatRec& r, int W, int H, int& bx0, int& by0,
+                                              int& bx1, int& by1) {
+  const float ux = r.a.x, uy = r.a.y, ex = r.b.w, ey = r.c.w;
+  const float fx0 = ceilf(ux - ex - 0.5f), fx1 = floorf(ux + ex - 0.5f);
+  const float fy0 = ceilf(uy - ey - 0.5f), fy1 = floorf(uy + ey - 0.5f);
+  const int x0 = (int)fmaxf(fx0, 0.f), x1 = (int)fminf(fx1, (float)(W - 1));
+  const int y0 = (int)fmaxf(fy0, 0.f), y1 = (int)fminf(fy1, (float)(H - 1));
+  if (!(fx0 <= fx1) || !(fy0 <= fy1) || x0 > x1 || y0 > y1) return false;
+  bx0 = x0 >> 4; bx1 = x1 >> 4; by0 = y0 >> 4; by1 = y1 >> 4;
+  return true;
+}
+
+__global__ void __launch_bounds__(kBinThreads) bin_kernel(
+    const uint32_t* __restrict__ sorted_ids, const SplatRec* __restrict__ rec,
+    SplatRec* __restrict__ rec_sorted, float4* __restrict__ g2d, Header* __restrict__ hdr,
+    unsigned long long* __restrict__ scan_status, const uint32_t* __restrict__ epoch,
+    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, uint32_t pair_cap, int W,
+    int H, int gw, int pair_passes) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_cnt[kBinTile];    // counts, then exclusive offsets
+  __shared__ uint32_t s_org[kBinTile];    // bx0 | by0 << 16
+  __shared__ uint16_t s_w[kBinTile];      // box width in blocks
+  __shared__ uint32_t s_hist[4][256];
+  __shared__ uint32_t s_warp[kBinThreads / 32];
+  __shared__ unsigned long long s_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
+  const uint32_t V = hdr->visible;
+  const uint32_t ntiles = (V + kBinTile - 1) / kBinTile;
+  const uint32_t tag = *epoch;
+  // persistent over tiles taken in order (look-back waits only on lower tiles)
+  for (;;) {
+  if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter[8], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= ntiles) break;
+  const uint32_t base = tile * kBinTile;
+
+  // 1-2: gather records into depth order, count blocks
+#pragma unroll
+  for (int k = 0; k < kBinItems; ++k) {
+    const int j = k * kBinThreads + tid;
+    const uint32_t r = base + j;
+    uint32_t cnt = 0, org = 0, w = 0;
+    if (r < V) {
+      const SplatRec R = rec[sorted_ids[r]];
+      rec_sorted[r] = R;
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      g2d[3 * (size_t)r] = z;
+      g2d[3 * (size_t)r + 1] = z;
+      g2d[3 * (size_t)r + 2] = z;
+      int bx0, by0, bx1, by1;
+      if (record_blocks(R, W, H, bx0, by0, bx1, by1)) {
+        w = bx1 - bx0 + 1;
+        cnt = w * (by1 - by0 + 1);
+        org = (uint32_t)bx0 | ((uint32_t)by0 << 16);
+      }
+    }
+    s_cnt[j] = cnt;
+    s_org[j] = org;
+    s_w[j] = (uint16_t)w;
+  }
+  __syncthreads();
+  // exclusive scan of the 1024 counts in rank order: 4 contiguous per thread
+  uint32_t c4[kBinItems], sum = 0;
+#pragma unroll
+  for (int k = 0; k < kBinItems; ++k) {
+    c4[k] = s_cnt[tid * kBinItems + k];
+    sum += c4[k];
+  }
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t wbefore = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kBinThreads / 32; ++w) {
+    const uint32_t v = s_warp[w];
+    if (w < warp) wbefore += v;
+    total += v;
+  }
+  uint32_t run = wbefore + x - sum;
+#pragma unroll
+  for (int k = 0; k < kBinItems; ++k) {
+    s_cnt[tid * kBinItems + k] = run;
+    run += c4[k];
+  }
+  // tile offset by decoupled look-back over lower tiles
+  if (tid == 0) {
+    unsigned long long* my = scan_status + tile;
+    unsigned long long excl = 0;
+    const unsigned long long tot = min((unsigned long long)total, kBinCount);
+    if (tile == 0) {
+      st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | tot);
+    } else {
+      st_relaxed64(my, ((unsigned long long)tag << 32) | kBinAgg | tot);
+      int64_t j = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const unsigned long long s = ld_relaxed64(scan_status + j);
+        const bool ready = (uint32_t)(s >> 32) == tag && (s & (3ull << 30)) != 0;
+        if (!ready) {
+          if (++spins > kSpinLimit) {
+            atomicOr(&hdr->status, kStatusTimeout);
+            break;
+          }
+          continue;
+        }
+        excl += s & kBinCount;
+        if ((s & (3ull << 30)) == kBinPre) break;
+        --j;
+      }
+      st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | min(excl + tot, kBinCount));
+    }
+    s_off = excl;
+    if (base + kBinTile >= V) {  // last tile: total pair count
+      const unsigned long long want = excl + total;
+      hdr->pairs_wanted = (uint32_t)min(want, (unsigned long long)0xFFFFFFFFu);
+      hdr->pairs = (uint32_t)min(want, (unsigned long long)pair_cap);
+      if (want > pair_cap) atomicOr(&hdr->status, kStatusCapacity);
+    }
+  }
+  __syncthreads();
+  const unsigned long long off = s_off;
+  // 3-4: emit the tile's pairs, all threads sharing the work
+  for (uint32_t p = tid; p < total; p += kBinThreads) {
+    int lo = 0, hi = kBinTile;  // last j with s_cnt[j] <= p
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_cnt[mid] <= p) lo = mid; else hi = mid;
+    }
+    const uint32_t k = p - s_cnt[lo];
+    const uint32_t w = s_w[lo];
+    const uint32_t org = s_org[lo];
+    const uint32_t bx = (org & 0xFFFFu) + k % w;
+    const uint32_t by = (org >> 16) + k / w;
+    const uint32_t key = by * (uint32_t)gw + bx;
+    const unsigned long long pos = off + p;
+    if (pos < pair_cap) {
+      pair_keys[pos] = key;
+      pair_vals[pos] = base + lo;
+      for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
+    }
+  }
+  __syncthreads();
+  }
+  for (int i = tid; i < pair_passes * 256; i += kBinThreads) {
+    const uint32_t v = (&s_hist[0][0])[i];
+    if (v) atomicAdd(&hdr->pair_hist[0][0] + i, v);
+  }
+}
+
+// Block ranges [start, end) in the pairs sorted by block id.  ranges must be
+// zero beforehand (the projection kernel clears them).
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys,
+                                                     const Header* __restrict__ hdr,
+                                                     uint2* __restrict__ ranges) {
+  const uint32_t P = hdr->pairs;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+    if (i + 1 == P || keys[i + 1] != k) ranges[k].y = i + 1;
+  }
+}
+
+cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, SplatRec* rec_sorted,
+                       float* g2d, Header* hdr, unsigned long long* scan_status,
+                       const uint32_t* epoch, uint32_t* pair_keys, uint32_t* pair_vals,
+                       uint32_t pair_cap, int W, int H, int gw, int pair_passes, int n_cap,
+                       int grid_cap, cudaStream_t st) {
+  int tiles = (n_cap + kBinTile - 1) / kBinTile;
+  if (tiles == 0) return cudaSuccess;
+  if (tiles > grid_cap) tiles = grid_cap;
+  bin_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, rec_sorted,
+                                            reinterpret_cast<float4*>(g2d), hdr, scan_status, epoch,
+                                            pair_keys, pair_vals, pair_cap, W, H, gw, pair_passes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges, int num_sms,
+                          cudaStream_t st) {
+  ranges_kernel<<<num_sms * 8, 256, 0, st>>>(keys, hdr, ranges);
+  return cudaGetLastError();
+}
+
+size_t bin_tiles(size_t n) { return (n + kBinTile - 1) / kBinTile; }
+
+}  // namespace gsr

@@ -1,0 +1,419 @@
+// Per-splat projection (forward) and its chain rule (backward).
+//
+// Forward (Sec. 2.1.1 Eq. 1, Sec. 2.1.2): t = W mu + w; cull tz <= znear;
+// Sigma_3D = R S S^T R^T; Sigma_2D = J W Sigma_3D W^T J^T + 0.3 I;
+// conic = Sigma_2D^-1; mu_2D = (fx tx/tz + cx, fy ty/tz + cy); SH colour; the
+// alpha >= 1/255 ellipse's bounding box (the screen quad the paper rasterizes)
+// and an off-screen / opacity-floor cull.  Writes the 48-B record, the depth
+// key (FP32 bits of tz, or 0xFFFFFFFF when culled), the visible count and the
+// four 8-bit digit histograms the depth sort needs.
+//
+// Backward: from the per-splat 2D gradients accumulated by the backward raster
+// (mu_2D, conic, colour, opacity) to mean, scale, quaternion, opacity and SH
+// gradients, added into the caller's buffers.
+#include "common.cuh"
+
+namespace gsr {
+
+struct CamDev {
+  float R[9];
+  float t[3];
+  float campos[3];
+  float fx, fy, cx, cy;
+  int W, H;
+  float znear;
+};
+
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float* R) {
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Shared by forward and backward: everything up to Sigma_2D.
+struct ProjState {
+  float t[3];
+  float qn[4], rq;       // normalised quaternion, 1/|q|
+  float R[9];            // rotation
+  float M[9];            // R diag(s)
+  float S3[6];           // Sigma_3D (xx, xy, xz, yy, yz, zz)
+  float Tm[6];           // J W (2x3)
+  float s2[3];           // Sigma_2D (00, 01, 11)
+};
+
+__device__ __forceinline__ bool project_core(const CamDev& cam, float mx, float my, float mz,
+                                             float4 q, float sx, float sy, float sz,
+                                             ProjState& ps) {
+  ps.t[0] = cam.R[0] * mx + cam.R[1] * my + cam.R[2] * mz + cam.t[0];
+  ps.t[1] = cam.R[3] * mx + cam.R[4] * my + cam.R[5] * mz + cam.t[1];
+  ps.t[2] = cam.R[6] * mx + cam.R[7] * my + cam.R[8] * mz + cam.t[2];
+  if (!(ps.t[2] > cam.znear)) return false;
+  const float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  if (!(qq > 0.f)) return false;
+  ps.rq = rsqrtf(qq);
+  ps.qn[0] = q.x * ps.rq;
+  ps.qn[1] = q.y * ps.rq;
+  ps.qn[2] = q.z * ps.rq;
+  ps.qn[3] = q.w * ps.rq;
+  quat_to_rot(ps.qn[0], ps.qn[1], ps.qn[2], ps.qn[3], ps.R);
+  const float s[3] = {sx, sy, sz};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ps.M[i * 3 + j] = ps.R[i * 3 + j] * s[j];
+  float S[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      S[i][j] = ps.M[i * 3 + 0] * ps.M[j * 3 + 0] + ps.M[i * 3 + 1] * ps.M[j * 3 + 1] +
+                ps.M[i * 3 + 2] * ps.M[j * 3 + 2];
+  ps.S3[0] = S[0][0]; ps.S3[1] = S[0][1]; ps.S3[2] = S[0][2];
+  ps.S3[3] = S[1][1]; ps.S3[4] = S[1][2]; ps.S3[5] = S[2][2];
+  const float iz = 1.f / ps.t[2];
+  const float J00 = cam.fx * iz, J02 = -cam.fx * ps.t[0] * iz * iz;
+  const float J11 = cam.fy * iz, J12 = -cam.fy * ps.t[1] * iz * iz;
+  // Tm = J W
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    ps.Tm[j] = J00 * cam.R[j] + J02 * cam.R[6 + j];
+    ps.Tm[3 + j] = J11 * cam.R[3 + j] + J12 * cam.R[6 + j];
+  }
+  // Sigma_2D = Tm S Tm^T + 0.3 I
+  float TS[2][3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      TS[i][j] = ps.Tm[i * 3 + 0] * S[0][j] + ps.Tm[i * 3 + 1] * S[1][j] + ps.Tm[i * 3 + 2] * S[2][j];
+  ps.s2[0] = TS[0][0] * ps.Tm[0] + TS[0][1] * ps.Tm[1] + TS[0][2] * ps.Tm[2] + kDilation;
+  ps.s2[1] = TS[0][0] * ps.Tm[3] + TS[0][1] * ps.Tm[4] + TS[0][2] * ps.Tm[5];
+  ps.s2[2] = TS[1][0] * ps.Tm[3] + TS[1][1] * ps.Tm[4] + TS[1][2] * ps.Tm[5] + kDilation;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Forward projection.  Persistent grid-stride loop so that each CTA flushes
+// its shared-memory digit histograms to global memory once.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) project_fwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float4* __restrict__ quats, const float* __restrict__ opac,
+    const float* __restrict__ sh, int n, int deg, CamDev cam, int clamp01,
+    SplatRec* __restrict__ rec, uint32_t* __restrict__ keys, Header* __restrict__ hdr,
+    uint2* __restrict__ ranges, int n_ranges, uint32_t* __restrict__ epoch) {
+  __shared__ uint32_t s_hist[4][256];
+  // a new view: look-back status words of earlier views stop matching
+  if (blockIdx.x == 0 && threadIdx.x == 0) *epoch += 1u;
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  // zero the block ranges for this view (rebuilt by the binning stage)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ranges; i += gridDim.x * blockDim.x)
+    ranges[i] = make_uint2(0, 0);
+  __syncthreads();
+  const int K = (deg + 1) * (deg + 1);
+  uint32_t local_visible = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t key = kNone;
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const float o = opac[i];
+    ProjState ps;
+    bool ok = o * 255.0f >= 1.0f;   // opacity floor: alpha <= o < 1/255 everywhere
+    if (ok) ok = project_core(cam, mx, my, mz, quats[i], scales[3 * i], scales[3 * i + 1],
+                              scales[3 * i + 2], ps);
+    float det = 0.f;
+    if (ok) {
+      det = ps.s2[0] * ps.s2[2] - ps.s2[1] * ps.s2[1];
+      ok = det > 0.f;
+    }
+    if (ok) {
+      const float idet = 1.f / det;
+      const float ca = ps.s2[2] * idet, cb = -ps.s2[1] * idet, cc = ps.s2[0] * idet;
+      const float iz = 1.f / ps.t[2];
+      const float ux = cam.fx * ps.t[0] * iz + cam.cx;
+      const float uy = cam.fy * ps.t[1] * iz + cam.cy;
+      // power >= -ln(255 o)  <=>  d^T Q d <= k = 2 ln(255 o); the ellipse's box
+      // has half-widths sqrt(k Sigma_00), sqrt(k Sigma_11).  A small relative
+      // and absolute widening keeps every fragment the FP32 raster accepts.
+      const float thr = -log2f(255.0f * o);
+      const float k = fmaxf(0.f, -2.0f * kLn2 * thr);
+      const float ex = sqrtf(k * ps.s2[0]) * 1.002f + 0.02f;
+      const float ey = sqrtf(k * ps.s2[2]) * 1.002f + 0.02f;
+      // any pixel centre (x + 0.5, y + 0.5) inside the box?
+      const float x0 = ceilf(ux - ex - 0.5f), x1 = floorf(ux + ex - 0.5f);
+      const float y0 = ceilf(uy - ey - 0.5f), y1 = floorf(uy + ey - 0.5f);
+      ok = x0 <= x1 && y0 <= y1 && x1 >= 0.f && y1 >= 0.f && x0 <= (float)(cam.W - 1) &&
+           y0 <= (float)(cam.H - 1);
+      if (ok) {
+        // colour from SH at the view direction
+        float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+        const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+        vx *= rn; vy *= rn; vz *= rn;
+        float Y[16];
+        sh_eval(deg, vx, vy, vz, Y);
+        const float* shp = sh + (size_t)i * K * 3;
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        for (int kk = 0; kk < K; ++kk) {
+          col[0] += shp[kk * 3 + 0] * Y[kk];
+          col[1] += shp[kk * 3 + 1] * Y[kk];
+          col[2] += shp[kk * 3 + 2] * Y[kk];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          col[c] = fmaxf(0.f, col[c]);
+          if (clamp01) col[c] = fminf(1.f, col[c]);
+        }
+        SplatRec r;
+        r.a = make_float4(ux, uy, -0.5f * kLog2e * ca, -kLog2e * cb);
+        r.b = make_float4(-0.5f * kLog2e * cc, thr, o, ex);
+        r.c = make_float4(col[0], col[1], col[2], ey);
+        rec[i] = r;
+        key = __float_as_uint(ps.t[2]);
+        local_visible++;
+        atomicAdd(&s_hist[0][key & 0xFF], 1u);
+        atomicAdd(&s_hist[1][(key >> 8) & 0xFF], 1u);
+        atomicAdd(&s_hist[2][(key >> 16) & 0xFF], 1u);
+        atomicAdd(&s_hist[3][key >> 24], 1u);
+      }
+    }
+    keys[i] = key;
+  }
+  // visible count: warp-aggregate, one atomic per warp
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) local_visible += __shfl_xor_sync(0xffffffffu, local_visible, off);
+  if ((threadIdx.x & 31) == 0 && local_visible) atomicAdd(&hdr->visible, local_visible);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    const uint32_t v = (&s_hist[0][0])[i];
+    if (v) atomicAdd(&hdr->depth_hist[0][0] + i, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Backward projection: one thread per visible depth rank.
+// g2 (12 floats per rank): U_x, U_y, S_xx, S_xy, S_yy, dr, dg, db, do, -, -, -
+// accumulated by the raster with the prescaled conic; converted here:
+//   dL/dmu_2D = -ln2 (U_x, U_y), dL/da = -S_xx / 2, dL/db = -S_xy, dL/dc = -S_yy / 2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void project_bwd_one(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float4* __restrict__ quats, const float* __restrict__ opac,
+    const float* __restrict__ sh, int deg, const CamDev& cam, int clamp01,
+    const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ g2d, uint32_t r,
+    float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
+    float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  const float4 ga = g2d[3 * r], gb = g2d[3 * r + 1], gc = g2d[3 * r + 2];
+  if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
+      gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
+    return;  // no fragment of this splat received a gradient
+  const uint32_t id = sorted_ids[r];
+  const float mx = means[3 * id], my = means[3 * id + 1], mz = means[3 * id + 2];
+  const float sx = scales[3 * id], sy = scales[3 * id + 1], sz = scales[3 * id + 2];
+  ProjState ps;
+  project_core(cam, mx, my, mz, quats[id], sx, sy, sz, ps);
+  const float det = ps.s2[0] * ps.s2[2] - ps.s2[1] * ps.s2[1];
+  const float idet = 1.f / det;
+  const float qa = ps.s2[2] * idet, qb = -ps.s2[1] * idet, qc = ps.s2[0] * idet;
+  // 2D gradients in natural units
+  const float gmu2x = -kLn2 * ga.x, gmu2y = -kLn2 * ga.y;
+  const float gA = -0.5f * ga.z, gB = -ga.w, gC = -0.5f * gb.x;
+  const float grgb[3] = {gb.y, gb.z, gb.w};
+  const float gop = gc.x;
+  float gmu[3] = {0.f, 0.f, 0.f};
+
+  // colour: rgb = clamp(sum sh Y + 0.5)
+  {
+    const int K = (deg + 1) * (deg + 1);
+    float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+    const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float dx = vx * rn, dy = vy * rn, dz = vz * rn;
+    float Y[16];
+    sh_eval(deg, dx, dy, dz, Y);
+    const float* shp = sh + (size_t)id * K * 3;
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < K; ++k) {
+      raw[0] += shp[k * 3 + 0] * Y[k];
+      raw[1] += shp[k * 3 + 1] * Y[k];
+      raw[2] += shp[k * 3 + 2] * Y[k];
+    }
+    float graw[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const bool pass = raw[c] > 0.f && (!clamp01 || raw[c] < 1.f);
+      graw[c] = pass ? grgb[c] : 0.f;
+    }
+    float* dsh = d_sh + (size_t)id * K * 3;
+    for (int k = 0; k < K; ++k) {
+      dsh[k * 3 + 0] += Y[k] * graw[0];
+      dsh[k * 3 + 1] += Y[k] * graw[1];
+      dsh[k * 3 + 2] += Y[k] * graw[2];
+    }
+    if (deg > 0) {
+      float dY[48];
+      sh_grad(deg, dx, dy, dz, dY);
+      float gd[3] = {0.f, 0.f, 0.f};
+      for (int k = 1; k < K; ++k) {
+        const float w = shp[k * 3 + 0] * graw[0] + shp[k * 3 + 1] * graw[1] + shp[k * 3 + 2] * graw[2];
+        gd[0] += w * dY[k * 3 + 0];
+        gd[1] += w * dY[k * 3 + 1];
+        gd[2] += w * dY[k * 3 + 2];
+      }
+      const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+      gmu[0] += (gd[0] - dx * dd) * rn;
+      gmu[1] += (gd[1] - dy * dd) * rn;
+      gmu[2] += (gd[2] - dz * dd) * rn;
+    }
+  }
+
+  // conic -> Sigma_2D: G_S = -Q G_Q Q, G_Q = [[gA, gB/2], [gB/2, gC]]
+  float GS00, GS01, GS11;
+  {
+    const float h = 0.5f * gB;
+    const float t00 = qa * gA + qb * h, t01 = qa * h + qb * gC;
+    const float t10 = qb * gA + qc * h, t11 = qb * h + qc * gC;
+    GS00 = -(t00 * qa + t01 * qb);
+    GS01 = -(t00 * qb + t01 * qc);
+    GS11 = -(t10 * qb + t11 * qc);
+  }
+  // Sigma_2D = Tm S3 Tm^T + 0.3 I:  G_S3 = Tm^T G_S Tm, G_Tm = 2 G_S Tm S3
+  const float* T = ps.Tm;
+  float GS3[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      GS3[i][j] = T[i] * (GS00 * T[j] + GS01 * T[3 + j]) + T[3 + i] * (GS01 * T[j] + GS11 * T[3 + j]);
+  const float S3[3][3] = {{ps.S3[0], ps.S3[1], ps.S3[2]},
+                          {ps.S3[1], ps.S3[3], ps.S3[4]},
+                          {ps.S3[2], ps.S3[4], ps.S3[5]}};
+  float TS[2][3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      TS[i][j] = T[i * 3] * S3[0][j] + T[i * 3 + 1] * S3[1][j] + T[i * 3 + 2] * S3[2][j];
+  float GT[2][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    GT[0][j] = 2.f * (GS00 * TS[0][j] + GS01 * TS[1][j]);
+    GT[1][j] = 2.f * (GS01 * TS[0][j] + GS11 * TS[1][j]);
+  }
+  // Tm = J W:  G_J = G_Tm W^T (only J00, J02, J11, J12 depend on t)
+  const float* W = cam.R;
+  const float GJ00 = GT[0][0] * W[0] + GT[0][1] * W[1] + GT[0][2] * W[2];
+  const float GJ02 = GT[0][0] * W[6] + GT[0][1] * W[7] + GT[0][2] * W[8];
+  const float GJ11 = GT[1][0] * W[3] + GT[1][1] * W[4] + GT[1][2] * W[5];
+  const float GJ12 = GT[1][0] * W[6] + GT[1][1] * W[7] + GT[1][2] * W[8];
+  const float tx = ps.t[0], ty = ps.t[1], tz = ps.t[2];
+  const float iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+  float gt[3];
+  gt[0] = GJ02 * (-cam.fx * iz2) + gmu2x * cam.fx * iz;
+  gt[1] = GJ12 * (-cam.fy * iz2) + gmu2y * cam.fy * iz;
+  gt[2] = GJ00 * (-cam.fx * iz2) + GJ02 * (2.f * cam.fx * tx * iz3) + GJ11 * (-cam.fy * iz2) +
+          GJ12 * (2.f * cam.fy * ty * iz3) - gmu2x * cam.fx * tx * iz2 - gmu2y * cam.fy * ty * iz2;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt[0] + W[3 + j] * gt[1] + W[6 + j] * gt[2];
+
+  // Sigma_3D = M M^T: G_M = 2 G_S3 M; M_ij = R_ij s_j
+  const float s[3] = {sx, sy, sz};
+  float gs[3] = {0.f, 0.f, 0.f};
+  float GR[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float gm = 2.f * (GS3[i][0] * ps.M[j] + GS3[i][1] * ps.M[3 + j] + GS3[i][2] * ps.M[6 + j]);
+      gs[j] += ps.R[i * 3 + j] * gm;
+      GR[i * 3 + j] = gm * s[j];
+    }
+  // R(q_hat) -> q_hat -> q
+  const float w = ps.qn[0], x = ps.qn[1], y = ps.qn[2], z = ps.qn[3];
+  float gq[4];
+  gq[0] = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+  gq[1] = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] +
+                 w * GR[7] - 2.f * x * GR[8]);
+  gq[2] = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] +
+                 z * GR[7] - 2.f * y * GR[8]);
+  gq[3] = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] +
+                 y * GR[5] + x * GR[6] + y * GR[7]);
+  const float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+  d_quats[4 * id + 0] += (gq[0] - w * qd) * ps.rq;
+  d_quats[4 * id + 1] += (gq[1] - x * qd) * ps.rq;
+  d_quats[4 * id + 2] += (gq[2] - y * qd) * ps.rq;
+  d_quats[4 * id + 3] += (gq[3] - z * qd) * ps.rq;
+  d_scales[3 * id + 0] += gs[0];
+  d_scales[3 * id + 1] += gs[1];
+  d_scales[3 * id + 2] += gs[2];
+  d_means[3 * id + 0] += gmu[0];
+  d_means[3 * id + 1] += gmu[1];
+  d_means[3 * id + 2] += gmu[2];
+  d_opac[id] += gop;
+}
+
+__global__ void __launch_bounds__(128) project_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float4* __restrict__ quats, const float* __restrict__ opac,
+    const float* __restrict__ sh, int deg, CamDev cam, int clamp01,
+    const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ g2d,
+    const Header* __restrict__ hdr, float* __restrict__ d_means, float* __restrict__ d_scales,
+    float* __restrict__ d_quats, float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  const uint32_t V = hdr->visible;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x)
+    project_bwd_one(means, scales, quats, opac, sh, deg, cam, clamp01, sorted_ids, g2d, r, d_means,
+                    d_scales, d_quats, d_opac, d_sh);
+}
+
+}  // namespace gsr
+
+// Host launchers (called from api.cu)
+namespace gsr {
+
+CamDev make_cam(const gs_camera& c) {
+  CamDev d;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) d.R[i * 3 + j] = c.viewmat[i * 4 + j];
+    d.t[i] = c.viewmat[i * 4 + 3];
+    d.campos[i] = c.campos[i];
+  }
+  d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+  d.W = c.width; d.H = c.height; d.znear = c.znear;
+  return d;
+}
+
+cudaError_t launch_project_fwd(const float* means, const float* scales, const float* quats,
+                               const float* opac, const float* sh, int n, int deg,
+                               const gs_camera& cam, int clamp01, SplatRec* rec, uint32_t* keys,
+                               Header* hdr, uint2* ranges, int n_ranges, uint32_t* epoch,
+                               int num_sms, cudaStream_t st) {
+  int blocks = (n + 255) / 256;
+  const int cap = num_sms * 8;  // persistent: a few waves' worth of CTAs
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  project_fwd_kernel<<<blocks, 256, 0, st>>>(means, scales, reinterpret_cast<const float4*>(quats),
+                                             opac, sh, n, deg, make_cam(cam), clamp01, rec, keys,
+                                             hdr, ranges, n_ranges, epoch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const float* means, const float* scales, const float* quats,
+                               const float* opac, const float* sh, int n_cap, int deg,
+                               const gs_camera& cam, int clamp01, const uint32_t* sorted_ids,
+                               const float* g2d, const Header* hdr, float* d_means,
+                               float* d_scales, float* d_quats, float* d_opac, float* d_sh,
+                               int num_sms, cudaStream_t st) {
+  int blocks = (n_cap + 127) / 128;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > num_sms * 16) blocks = num_sms * 16;
+  project_bwd_kernel<<<blocks, 128, 0, st>>>(
+      means, scales, reinterpret_cast<const float4*>(quats), opac, sh, deg, make_cam(cam), clamp01,
+      sorted_ids, reinterpret_cast<const float4*>(g2d), hdr, d_means, d_scales, d_quats, d_opac,
+      d_sh);
+  return cudaGetLastError();
+}
+
+}  // namespace gsr
