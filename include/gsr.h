@@ -237,8 +237,8 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
 
 /* Copies an internal array of `ws` into caller device memory `dst` (`bytes`):
  * GS_ARRAY_SORTED_IDS u32 [V], GS_ARRAY_DEPTH_KEYS u32 [n] (0xFFFFFFFF = culled),
- * GS_ARRAY_RECORDS float [n][12] (mu_x, mu_y, A, B, C, thr, o, ext_x, r, g, b,
- * ext_y with (A, B, C) = -log2(e) (a/2, b, c/2) of the conic and thr =
+ * GS_ARRAY_RECORDS float [n][12] (mu_x, mu_y, A, B, C, thr, o, ext_y, r, g, b,
+ * ext_x with (A, B, C) = -log2(e) (a/2, b, c/2) of the conic and thr =
  * log2(1/(255 o))), GS_ARRAY_PAIR_BLOCKS u32 [P], GS_ARRAY_PAIR_RANKS u32 [P]
  * (sorted by block), GS_ARRAY_RANGES u32 [blocks][2], GS_ARRAY_GRAD2D float
  * [V][12] (per depth rank: the backward's unscaled accumulators). */

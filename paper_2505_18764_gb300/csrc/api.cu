@@ -25,8 +25,8 @@ cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, ui
 cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
 cudaError_t launch_bin(const uint32_t*, const SplatRec*, SplatRec*, float*, Header*,
-                       unsigned long long*, const uint32_t*, uint32_t*, uint32_t*, uint32_t, int, int,
-                       int, int, int, int, cudaStream_t);
+                       unsigned long long*, const uint32_t*, uint32_t*, uint2*, uint32_t*, uint32_t*,
+                       uint32_t*, uint32_t, int, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, cudaStream_t);
 cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const SplatRec*, int, int, int, int,
                               float, int, float*, void*, uint32_t*, uint32_t*, cudaStream_t);
@@ -37,6 +37,7 @@ cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double
                         cudaStream_t);
 size_t sort_tiles(size_t n);
 size_t bin_tiles(size_t n);
+size_t emit_chunks(size_t pairs);
 
 namespace {
 
@@ -89,6 +90,9 @@ enum Slot {
   L_REC,         // [n] records by splat id
   L_REC_SORTED,  // [n] records by depth rank
   L_G2D,         // [n][12] backward accumulators by depth rank
+  L_OFFSETS,     // [n] first pair index of each depth rank
+  L_BOXES,       // [n] uint2 block box of each depth rank
+  L_CHUNKS,      // [pair_cap / 2048 + 1] first depth rank of each emission chunk
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
   L_END
@@ -121,6 +125,9 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_KEYS] = n_cap * 4;
   sz[L_KA] = sz[L_VA] = sz[L_KB] = sz[L_VB] = n_cap * 4;
   sz[L_REC] = sz[L_REC_SORTED] = sz[L_G2D] = n_cap * sizeof(SplatRec);
+  sz[L_OFFSETS] = n_cap * 4;
+  sz[L_BOXES] = n_cap * 8;
+  sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
   size_t o = 0;
@@ -304,6 +311,7 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
   const int grid_cap = num_sms() * kPersistentPerSm;
   GS_CUDA(launch_bin(at<uint32_t>(ws, L_VB), at<SplatRec>(ws, L_REC), at<SplatRec>(ws, L_REC_SORTED),
                      at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN), epoch,
+                     at<uint32_t>(ws, L_OFFSETS), at<uint2>(ws, L_BOXES), at<uint32_t>(ws, L_CHUNKS),
                      at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PVA), (uint32_t)ws->pair_cap,
                      cam->width, cam->height, gw, ws->pair_passes, ws->n, grid_cap, st),
           "bin kernel");

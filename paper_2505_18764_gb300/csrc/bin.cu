@@ -3,16 +3,18 @@
 // The paper rasterizes each depth-sorted splat as a screen quad bounding its
 // alpha >= 1/255 ellipse (Sec. 1, Sec. 2.2) into fixed O(N) buffers.  Here the
 // quad's pixel-centre box is turned into the list of 16x16 pixel blocks it
-// touches.  One fused kernel, one tile of 1024 depth ranks per CTA:
-//   1. gathers each splat's record into depth order (the raster reads
-//      records by rank) and zeroes its backward accumulators,
-//   2. counts its blocks and scans the counts across tiles with a decoupled
-//      look-back (tagged 64-bit status words, bounded waits),
-//   3. writes the pairs with all 256 threads sharing the tile's pairs
-//      (a binary search in the tile's scan finds each pair's splat), so one
-//      very large splat does not serialise on one thread,
-//   4. accumulates the 8-bit digit histograms of the block ids that the
-//      stable pair sort by block needs (depth order survives within a block).
+// touches.  Two passes:
+//   count: per tile of 1024 depth ranks, gathers each splat's record into
+//      depth order (the raster reads records by rank), zeroes its backward
+//      accumulators, counts its blocks and scans the counts across tiles with a
+//      decoupled look-back (tagged 64-bit status words, bounded waits), giving
+//      every rank its first pair index;
+//   emit: each CTA writes whole chunks of 2048 consecutive pairs (a binary
+//      search over the chunk's ranks in shared memory finds each pair's
+//      splat), so the work is even even though the nearest splats are the
+//      largest on screen; it also accumulates the 8-bit digit histograms of the
+//      block ids that the stable pair sort by block needs (depth order survives
+//      within a block).
 // Pairs beyond the capacity are not written; the shortfall is recorded.
 #include "common.cuh"
 
@@ -24,11 +26,12 @@ constexpr int kBinTile = kBinThreads * kBinItems;  // 1024 ranks
 constexpr unsigned long long kBinAgg = 1ull << 30;
 constexpr unsigned long long kBinPre = 2ull << 30;
 constexpr unsigned long long kBinCount = (1ull << 30) - 1;
+constexpr int kEmitChunk = 2048;  // pairs written per CTA step of the emission pass
 
 // Pixel-centre box of a record, clamped to the image, in block units.
 __device__ __forceinline__ bool record_blocks(const SplatRec& r, int W, int H, int& bx0, int& by0,
                                               int& bx1, int& by1) {
-  const float ux = r.a.x, uy = r.a.y, ex = r.b.w, ey = r.c.w;
+  const float ux = r.a.x, uy = r.a.y, ex = r.c.w, ey = r.b.w;
   const float fx0 = ceilf(ux - ex - 0.5f), fx1 = floorf(ux + ex - 0.5f);
   const float fy0 = ceilf(uy - ey - 0.5f), fy1 = floorf(uy + ey - 0.5f);
   const int x0 = (int)fmaxf(fx0, 0.f), x1 = (int)fminf(fx1, (float)(W - 1));
@@ -38,144 +41,176 @@ __device__ __forceinline__ bool record_blocks(const SplatRec& r, int W, int H, i
   return true;
 }
 
-__global__ void __launch_bounds__(kBinThreads) bin_kernel(
+// Pass 1: one tile of 1024 depth ranks per step of a persistent loop.
+__global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
     const uint32_t* __restrict__ sorted_ids, const SplatRec* __restrict__ rec,
     SplatRec* __restrict__ rec_sorted, float4* __restrict__ g2d, Header* __restrict__ hdr,
     unsigned long long* __restrict__ scan_status, const uint32_t* __restrict__ epoch,
-    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, uint32_t pair_cap, int W,
-    int H, int gw, int pair_passes) {
+    uint32_t* __restrict__ offsets, uint2* __restrict__ boxes, uint32_t* __restrict__ chunk_rank,
+    uint32_t pair_cap, int W, int H) {
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_cnt[kBinTile];    // counts, then exclusive offsets
-  __shared__ uint32_t s_org[kBinTile];    // bx0 | by0 << 16
-  __shared__ uint16_t s_w[kBinTile];      // box width in blocks
-  __shared__ uint32_t s_hist[4][256];
+  __shared__ uint32_t s_cnt[kBinTile];
   __shared__ uint32_t s_warp[kBinThreads / 32];
   __shared__ unsigned long long s_off;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
   const uint32_t V = hdr->visible;
   const uint32_t ntiles = (V + kBinTile - 1) / kBinTile;
   const uint32_t tag = *epoch;
-  // persistent over tiles taken in order (look-back waits only on lower tiles)
+  const uint32_t chunk_cap = (pair_cap + kEmitChunk - 1) / kEmitChunk;
   for (;;) {
-  if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter[8], 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  if (tile >= ntiles) break;
-  const uint32_t base = tile * kBinTile;
-
-  // 1-2: gather records into depth order, count blocks
+    if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter[8], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint32_t base = tile * kBinTile;
+    // gather records into depth order, zero the backward accumulators, count blocks
 #pragma unroll
-  for (int k = 0; k < kBinItems; ++k) {
-    const int j = k * kBinThreads + tid;
-    const uint32_t r = base + j;
-    uint32_t cnt = 0, org = 0, w = 0;
-    if (r < V) {
-      const SplatRec R = rec[sorted_ids[r]];
-      rec_sorted[r] = R;
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      g2d[3 * (size_t)r] = z;
-      g2d[3 * (size_t)r + 1] = z;
-      g2d[3 * (size_t)r + 2] = z;
-      int bx0, by0, bx1, by1;
-      if (record_blocks(R, W, H, bx0, by0, bx1, by1)) {
-        w = bx1 - bx0 + 1;
-        cnt = w * (by1 - by0 + 1);
-        org = (uint32_t)bx0 | ((uint32_t)by0 << 16);
-      }
-    }
-    s_cnt[j] = cnt;
-    s_org[j] = org;
-    s_w[j] = (uint16_t)w;
-  }
-  __syncthreads();
-  // exclusive scan of the 1024 counts in rank order: 4 contiguous per thread
-  uint32_t c4[kBinItems], sum = 0;
-#pragma unroll
-  for (int k = 0; k < kBinItems; ++k) {
-    c4[k] = s_cnt[tid * kBinItems + k];
-    sum += c4[k];
-  }
-  uint32_t x = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  uint32_t wbefore = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < kBinThreads / 32; ++w) {
-    const uint32_t v = s_warp[w];
-    if (w < warp) wbefore += v;
-    total += v;
-  }
-  uint32_t run = wbefore + x - sum;
-#pragma unroll
-  for (int k = 0; k < kBinItems; ++k) {
-    s_cnt[tid * kBinItems + k] = run;
-    run += c4[k];
-  }
-  // tile offset by decoupled look-back over lower tiles
-  if (tid == 0) {
-    unsigned long long* my = scan_status + tile;
-    unsigned long long excl = 0;
-    const unsigned long long tot = min((unsigned long long)total, kBinCount);
-    if (tile == 0) {
-      st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | tot);
-    } else {
-      st_relaxed64(my, ((unsigned long long)tag << 32) | kBinAgg | tot);
-      int64_t j = (int64_t)tile - 1;
-      uint32_t spins = 0;
-      while (j >= 0) {
-        const unsigned long long s = ld_relaxed64(scan_status + j);
-        const bool ready = (uint32_t)(s >> 32) == tag && (s & (3ull << 30)) != 0;
-        if (!ready) {
-          if (++spins > kSpinLimit) {
-            atomicOr(&hdr->status, kStatusTimeout);
-            break;
-          }
-          continue;
+    for (int k = 0; k < kBinItems; ++k) {
+      const int j = k * kBinThreads + tid;
+      const uint32_t r = base + j;
+      uint32_t cnt = 0;
+      if (r < V) {
+        const SplatRec R = rec[sorted_ids[r]];
+        rec_sorted[r] = R;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        g2d[3 * (size_t)r] = z;
+        g2d[3 * (size_t)r + 1] = z;
+        g2d[3 * (size_t)r + 2] = z;
+        int bx0, by0, bx1, by1;
+        uint2 box = make_uint2(0u, 0u);
+        if (record_blocks(R, W, H, bx0, by0, bx1, by1)) {
+          const uint32_t w = bx1 - bx0 + 1, h = by1 - by0 + 1;
+          cnt = w * h;
+          box = make_uint2((uint32_t)bx0 | ((uint32_t)by0 << 16), w | (h << 16));
         }
-        excl += s & kBinCount;
-        if ((s & (3ull << 30)) == kBinPre) break;
-        --j;
+        boxes[r] = box;
       }
-      st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | min(excl + tot, kBinCount));
+      s_cnt[j] = cnt;
     }
-    s_off = excl;
-    if (base + kBinTile >= V) {  // last tile: total pair count
-      const unsigned long long want = excl + total;
-      hdr->pairs_wanted = (uint32_t)min(want, (unsigned long long)0xFFFFFFFFu);
-      hdr->pairs = (uint32_t)min(want, (unsigned long long)pair_cap);
-      if (want > pair_cap) atomicOr(&hdr->status, kStatusCapacity);
+    __syncthreads();
+    // exclusive scan of the 1024 counts in rank order: 4 contiguous per thread
+    uint32_t c4[kBinItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kBinItems; ++k) {
+      c4[k] = s_cnt[tid * kBinItems + k];
+      sum += c4[k];
     }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t wbefore = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kBinThreads / 32; ++w) {
+      const uint32_t v = s_warp[w];
+      if (w < warp) wbefore += v;
+      total += v;
+    }
+    // tile offset by decoupled look-back over lower tiles
+    if (tid == 0) {
+      unsigned long long* my = scan_status + tile;
+      unsigned long long excl = 0;
+      const unsigned long long tot = min((unsigned long long)total, kBinCount);
+      if (tile == 0) {
+        st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | tot);
+      } else {
+        st_relaxed64(my, ((unsigned long long)tag << 32) | kBinAgg | tot);
+        int64_t j = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        while (j >= 0) {
+          const unsigned long long s = ld_relaxed64(scan_status + j);
+          const bool ready = (uint32_t)(s >> 32) == tag && (s & (3ull << 30)) != 0;
+          if (!ready) {
+            if (++spins > kSpinLimit) {
+              atomicOr(&hdr->status, kStatusTimeout);
+              break;
+            }
+            continue;
+          }
+          excl += s & kBinCount;
+          if ((s & (3ull << 30)) == kBinPre) break;
+          --j;
+        }
+        st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | min(excl + tot, kBinCount));
+      }
+      s_off = excl;
+      if (base + kBinTile >= V) {  // last tile: total pair count
+        const unsigned long long want = excl + total;
+        hdr->pairs_wanted = (uint32_t)min(want, (unsigned long long)0xFFFFFFFFu);
+        hdr->pairs = (uint32_t)min(want, (unsigned long long)pair_cap);
+        if (want > pair_cap) atomicOr(&hdr->status, kStatusCapacity);
+      }
+    }
+    __syncthreads();
+    // global exclusive offsets; each emission chunk boundary c * kEmitChunk lies in
+    // exactly one rank's pair range, and that rank records itself for the chunk
+    unsigned long long run = s_off + wbefore + x - sum;
+#pragma unroll
+    for (int k = 0; k < kBinItems; ++k) {
+      const uint32_t r = base + tid * kBinItems + k;
+      if (r < V) {
+        // saturated: only pairs below the capacity (< 2^30) are ever emitted
+        offsets[r] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
+        if (c4[k]) {
+          unsigned long long c = (run + kEmitChunk - 1) / kEmitChunk;
+          const unsigned long long end = run + c4[k];
+          for (; c * kEmitChunk < end && c < chunk_cap; ++c) chunk_rank[c] = r;
+        }
+      }
+      run += c4[k];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const unsigned long long off = s_off;
-  // 3-4: emit the tile's pairs, all threads sharing the work
-  for (uint32_t p = tid; p < total; p += kBinThreads) {
-    int lo = 0, hi = kBinTile;  // last j with s_cnt[j] <= p
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_cnt[mid] <= p) lo = mid; else hi = mid;
+}
+
+// Pass 2: every CTA writes whole chunks of kEmitChunk consecutive pairs, so the
+// work is even however the pairs are spread over splats.
+__global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
+    const uint32_t* __restrict__ offsets, const uint2* __restrict__ boxes,
+    const uint32_t* __restrict__ chunk_rank, Header* __restrict__ hdr,
+    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, int gw, int pair_passes) {
+  __shared__ uint32_t s_off[kEmitChunk + 1];
+  __shared__ uint2 s_box[kEmitChunk + 1];
+  __shared__ uint32_t s_hist[4][256];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
+  const uint32_t P = hdr->pairs, V = hdr->visible;
+  const uint32_t nchunks = (P + kEmitChunk - 1) / kEmitChunk;
+  for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint32_t p0 = c * kEmitChunk;
+    const uint32_t p1 = min(P, p0 + kEmitChunk);
+    const uint32_t r0 = chunk_rank[c];
+    // ranks overlapping [p0, p1): each has >= 1 pair, so at most kEmitChunk of them
+    const uint32_t r1 = (c + 1 < nchunks) ? chunk_rank[c + 1] : V - 1;
+    const uint32_t nr = min(r1 - r0 + 1, (uint32_t)kEmitChunk);
+    __syncthreads();
+    for (uint32_t i = tid; i < nr; i += kBinThreads) {
+      s_off[i] = offsets[r0 + i];
+      s_box[i] = boxes[r0 + i];
     }
-    const uint32_t k = p - s_cnt[lo];
-    const uint32_t w = s_w[lo];
-    const uint32_t org = s_org[lo];
-    const uint32_t bx = (org & 0xFFFFu) + k % w;
-    const uint32_t by = (org >> 16) + k / w;
-    const uint32_t key = by * (uint32_t)gw + bx;
-    const unsigned long long pos = off + p;
-    if (pos < pair_cap) {
-      pair_keys[pos] = key;
-      pair_vals[pos] = base + lo;
+    __syncthreads();
+    for (uint32_t p = p0 + tid; p < p1; p += kBinThreads) {
+      int lo = 0, hi = (int)nr;  // last i with s_off[i] <= p
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= p) lo = mid; else hi = mid;
+      }
+      const uint32_t k = p - s_off[lo];
+      const uint2 box = s_box[lo];
+      const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
+      const uint32_t bx = (box.x & 0xFFFFu) + k % w;
+      const uint32_t by = (box.x >> 16) + min(k / w, h - 1);  // stays inside the box
+      const uint32_t key = by * (uint32_t)gw + bx;
+      pair_keys[p] = key;
+      pair_vals[p] = r0 + lo;
       for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
     }
   }
   __syncthreads();
-  }
   for (int i = tid; i < pair_passes * 256; i += kBinThreads) {
     const uint32_t v = (&s_hist[0][0])[i];
     if (v) atomicAdd(&hdr->pair_hist[0][0] + i, v);
@@ -197,15 +232,23 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
 
 cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, SplatRec* rec_sorted,
                        float* g2d, Header* hdr, unsigned long long* scan_status,
-                       const uint32_t* epoch, uint32_t* pair_keys, uint32_t* pair_vals,
+                       const uint32_t* epoch, uint32_t* offsets, uint2* boxes,
+                       uint32_t* chunk_rank, uint32_t* pair_keys, uint32_t* pair_vals,
                        uint32_t pair_cap, int W, int H, int gw, int pair_passes, int n_cap,
                        int grid_cap, cudaStream_t st) {
   int tiles = (n_cap + kBinTile - 1) / kBinTile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > grid_cap) tiles = grid_cap;
-  bin_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, rec_sorted,
-                                            reinterpret_cast<float4*>(g2d), hdr, scan_status, epoch,
-                                            pair_keys, pair_vals, pair_cap, W, H, gw, pair_passes);
+  bin_count_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, rec_sorted,
+                                                  reinterpret_cast<float4*>(g2d), hdr, scan_status,
+                                                  epoch, offsets, boxes, chunk_rank, pair_cap, W, H);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int chunks = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
+  if (chunks > grid_cap) chunks = grid_cap;
+  if (chunks < 1) chunks = 1;
+  bin_emit_kernel<<<chunks, kBinThreads, 0, st>>>(offsets, boxes, chunk_rank, hdr, pair_keys,
+                                                  pair_vals, gw, pair_passes);
   return cudaGetLastError();
 }
 
@@ -216,5 +259,6 @@ cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges
 }
 
 size_t bin_tiles(size_t n) { return (n + kBinTile - 1) / kBinTile; }
+size_t emit_chunks(size_t pairs) { return (pairs + kEmitChunk - 1) / kEmitChunk; }
 
 }  // namespace gsr

@@ -40,7 +40,7 @@ struct Header {
 };
 
 // Projected splat record, 48 B (three float4):
-//   a = (mu_x, mu_y, A, B), b = (C, thr, o, ext_x), c = (r, g, b, ext_y)
+//   a = (mu_x, mu_y, A, B), b = (C, thr, o, ext_y), c = (r, g, b, ext_x)
 // with power2 = A dx^2 + B dx dy + C dy^2 = log2(e) * power, i.e.
 // (A, B, C) = -log2(e) * (a/2, b, c/2) of the conic [[a, b], [b, c]], and
 // thr = log2(1 / (255 o)): a fragment exists iff power2 >= thr (alpha >= 1/255).
@@ -77,6 +77,27 @@ __device__ __forceinline__ float frag_alpha(float opacity, float power2, float& 
 
 __device__ __forceinline__ float next_T(float T, float alpha) {
   return __fmul_rn(T, __fsub_rn(1.0f, alpha));
+}
+
+// Can any pixel centre of a warp's 16x2 strip hold a fragment of this splat?
+// The centres lie on two rows y = ys, ys + 1 and x in [xs, xs + 15]; along a
+// row, power2 is a concave quadratic in dx whose maximum over the segment is
+// at the clamped vertex.  The margin keeps the test conservative against the
+// rounding of frag_power2 (it only decides what to skip).
+__device__ __forceinline__ bool strip_may_hit(const float4& a, const float4& b, float xs,
+                                              float ys) {
+  const float X0 = xs - a.x, X1 = X0 + 15.0f;
+  const float slope = -0.5f * a.w * __frcp_rn(a.z);  // vertex dx = slope * dy (A < 0)
+  const float lim = b.y - 0.01f - 1e-3f * fabsf(b.y);
+  bool hit = false;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float Y = ys + (float)r - a.y;
+    const float dx = fminf(fmaxf(slope * Y, X0), X1);
+    const float f = (a.z * dx + a.w * Y) * dx + b.x * Y * Y;
+    hit |= f >= lim;
+  }
+  return hit;
 }
 
 // ---------------------------------------------------------------------------

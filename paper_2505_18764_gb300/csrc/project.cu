@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         }
         SplatRec r;
         r.a = make_float4(ux, uy, -0.5f * kLog2e * ca, -kLog2e * cb);
-        r.b = make_float4(-0.5f * kLog2e * cc, thr, o, ex);
-        r.c = make_float4(col[0], col[1], col[2], ey);
+        r.b = make_float4(-0.5f * kLog2e * cc, thr, o, ey);
+        r.c = make_float4(col[0], col[1], col[2], ex);
         rec[i] = r;
         key = __float_as_uint(ps.t[2]);
         local_visible++;

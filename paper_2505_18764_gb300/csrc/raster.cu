@@ -27,7 +27,26 @@
 namespace gsr {
 
 constexpr int kBatch = 256;   // records staged per round
-constexpr int kSub = 32;      // splats per backward partial-reduction round
+
+// Each warp owns a 16x2 strip of the block (lanes 0-15 the upper row, 16-31
+// the lower).  After a batch of records is staged, every lane tests one splat
+// against its warp's strip (strip_may_hit); the ballots give each warp a
+// bitmask of the splats that can touch its strip, and the warp walks only
+// those, in depth order.
+__device__ __forceinline__ void stage_batch(const uint32_t* __restrict__ pair_ranks,
+                                            const SplatRec* __restrict__ rec, uint32_t s,
+                                            uint32_t end, float4* s_a, float4* s_b, float4* s_c,
+                                            uint32_t* s_rank) {
+  const uint32_t i = s + threadIdx.x;
+  if (i < end) {
+    const uint32_t r = pair_ranks[i];
+    s_rank[threadIdx.x] = r;
+    const SplatRec R = rec[r];
+    s_a[threadIdx.x] = R.a;
+    s_b[threadIdx.x] = R.b;
+    s_c[threadIdx.x] = R.c;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Forward
@@ -41,30 +60,29 @@ __global__ void __launch_bounds__(kBlockPixels) raster_fwd_kernel(
   __shared__ float4 s_b[kBatch];
   __shared__ float4 s_c[kBatch];
   __shared__ uint32_t s_rank[kBatch];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bx = blockIdx.x % gw, by = blockIdx.x / gw;
-  const int x = bx * kBlock + (tid & 15), y = by * kBlock + (tid >> 4);
+  const int x = bx * kBlock + (lane & 15), y = by * kBlock + 2 * warp + (lane >> 4);
   const bool inside = x < W && y < H;
   const uint2 range = ranges[blockIdx.x];
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const float xs = (float)(bx * kBlock) + 0.5f, ys = (float)(by * kBlock + 2 * warp) + 0.5f;
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   uint32_t last = kNone, n = 0;
   bool done = !inside;
   for (uint32_t s = range.x; s < range.y; s += kBatch) {
     if (__syncthreads_and(done)) break;
-    const uint32_t i = s + tid;
-    if (i < range.y) {
-      const uint32_t r = pair_ranks[i];
-      s_rank[tid] = r;
-      const SplatRec R = rec[r];
-      s_a[tid] = R.a;
-      s_b[tid] = R.b;
-      s_c[tid] = R.c;
-    }
+    stage_batch(pair_ranks, rec, s, range.y, s_a, s_b, s_c, s_rank);
     __syncthreads();
     const int cnt = min((uint32_t)kBatch, range.y - s);
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
+    for (int k = 0; k * 32 < cnt; ++k) {
+      const int jt = k * 32 + lane;
+      uint32_t m = __ballot_sync(0xffffffffu, jt < cnt && strip_may_hit(s_a[jt], s_b[jt], xs, ys));
+      if (__all_sync(0xffffffffu, done)) break;
+      while (m) {
+        const int j = k * 32 + __ffs(m) - 1;
+        m &= m - 1;
+        if (done) continue;
         const float4 a = s_a[j];
         const float4 b = s_b[j];
         float dx, dy;
@@ -80,10 +98,7 @@ __global__ void __launch_bounds__(kBlockPixels) raster_fwd_kernel(
         T = next_T(T, alpha);
         last = s_rank[j];
         ++n;
-        if (T < t_cull) {                  // every later fragment is T-culled
-          done = true;
-          break;
-        }
+        if (T < t_cull) done = true;       // every later fragment is T-culled
       }
     }
   }
@@ -149,18 +164,21 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
     const SplatRec* __restrict__ rec, int W, int H, int gw, float t_cull, int fmt,
     const void* __restrict__ state, const uint32_t* __restrict__ last_in,
     const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold) {
+  constexpr int kWarps = kBlockPixels / 32;
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float4 s_c[kBatch];
   __shared__ uint32_t s_rank[kBatch];
-  __shared__ __align__(16) float s_part[kSub][kBlockPixels / 32][12];
+  __shared__ __align__(16) float s_part[32][kWarps][12];
+  __shared__ uint32_t s_mask[kWarps];
   __shared__ uint32_t s_end;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bx = blockIdx.x % gw, by = blockIdx.x / gw;
-  const int x = bx * kBlock + (tid & 15), y = by * kBlock + (tid >> 4);
+  const int x = bx * kBlock + (lane & 15), y = by * kBlock + 2 * warp + (lane >> 4);
   const bool inside = x < W && y < H;
   const uint2 range = ranges[blockIdx.x];
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const float xs = (float)(bx * kBlock) + 0.5f, ys = (float)(by * kBlock + 2 * warp) + 0.5f;
   const int slot = transpose_slot(lane);
 
   float Cp0 = 0.f, Cp1 = 0.f, Cp2 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
@@ -175,7 +193,7 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
   }
   if (tid == 0) s_end = 0;
   // padding slots 9..11 of the partial sums stay zero
-  for (int i = tid; i < kSub * (kBlockPixels / 32); i += kBlockPixels) {
+  for (int i = tid; i < 32 * kWarps; i += kBlockPixels) {
     float* p = &s_part[0][0][0] + i * 12;
     p[9] = 0.f; p[10] = 0.f; p[11] = 0.f;
   }
@@ -188,60 +206,61 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
 
   for (uint32_t s = range.x; s < range.y; s += kBatch) {
     if (__syncthreads_and(done)) break;
-    const uint32_t i = s + tid;
-    if (i < range.y) {
-      const uint32_t r = pair_ranks[i];
-      s_rank[tid] = r;
-      const SplatRec R = rec[r];
-      s_a[tid] = R.a;
-      s_b[tid] = R.b;
-      s_c[tid] = R.c;
-    }
+    stage_batch(pair_ranks, rec, s, range.y, s_a, s_b, s_c, s_rank);
     __syncthreads();
     if (s_rank[0] >= block_end) break;   // uniform: ranks ascend within the block
     const int cnt = min((uint32_t)kBatch, range.y - s);
-    for (int j0 = 0; j0 < cnt; j0 += kSub) {
-      const int jn = min(kSub, cnt - j0);
-      for (int jj = 0; jj < jn; ++jj) {
-        const int j = j0 + jj;
+    for (int k = 0; k * 32 < cnt; ++k) {
+      const int jt = k * 32 + lane;
+      uint32_t m = __ballot_sync(0xffffffffu, jt < cnt && strip_may_hit(s_a[jt], s_b[jt], xs, ys));
+      if (__all_sync(0xffffffffu, done)) m = 0u;
+      if (MODE != GS_REDUCE_NAIVE && lane == 0) s_mask[warp] = m;
+      while (m) {
+        const int jj = __ffs(m) - 1;
+        m &= m - 1;
+        const int j = k * 32 + jj;
         float v[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
         bool frag = false;
         if (!done) {
-          const float4 a = s_a[j];
-          const float4 b = s_b[j];
-          float dx, dy;
-          const float p2 = frag_power2(px, py, a, b.x, dx, dy);
-          if (p2 >= b.y) {
-            frag = true;
-            float G, at;
-            const float alpha = frag_alpha(b.z, p2, G, at);
-            const float4 c = s_c[j];
-            const float oma = __fsub_rn(1.0f, alpha);
-            const float wT = __fmul_rn(alpha, T);
-            // Eq. 3
-            v[5] = g0 * wT;
-            v[6] = g1 * wT;
-            v[7] = g2 * wT;
-            // Eq. 7 with C'_i before its update
-            const float dLda = (g0 * (c.x * T - Cp0) + g1 * (c.y * T - Cp1) + g2 * (c.z * T - Cp2)) *
-                               __frcp_rn(oma);
-            // Eq. 6, Eq. 5
-            Cp0 -= wT * c.x;
-            Cp1 -= wT * c.y;
-            Cp2 -= wT * c.z;
-            T = next_T(T, alpha);
-            if (T < t_cull) done = true;
-            // alpha = min(0.99, o G): no gradient through the clamp
-            const float d_at = at < kAlphaMax ? dLda : 0.f;
-            v[8] = G * d_at;
-            const float w = at * d_at;
-            v[0] = w * (2.f * a.z * dx + a.w * dy);
-            v[1] = w * (a.w * dx + 2.f * b.x * dy);
-            v[2] = w * dx * dx;
-            v[3] = w * dx * dy;
-            v[4] = w * dy * dy;
+          if (s_rank[j] >= my_end) {
+            done = true;                   // past this pixel's last fragment
+          } else {
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+            float dx, dy;
+            const float p2 = frag_power2(px, py, a, b.x, dx, dy);
+            if (p2 >= b.y) {
+              frag = true;
+              float G, at;
+              const float alpha = frag_alpha(b.z, p2, G, at);
+              const float4 c = s_c[j];
+              const float oma = __fsub_rn(1.0f, alpha);
+              const float wT = __fmul_rn(alpha, T);
+              // Eq. 3
+              v[5] = g0 * wT;
+              v[6] = g1 * wT;
+              v[7] = g2 * wT;
+              // Eq. 7 with C'_i before its update
+              const float dLda = (g0 * (c.x * T - Cp0) + g1 * (c.y * T - Cp1) + g2 * (c.z * T - Cp2)) *
+                                 __frcp_rn(oma);
+              // Eq. 6, Eq. 5
+              Cp0 -= wT * c.x;
+              Cp1 -= wT * c.y;
+              Cp2 -= wT * c.z;
+              T = next_T(T, alpha);
+              if (T < t_cull) done = true;
+              // alpha = min(0.99, o G): no gradient through the clamp
+              const float d_at = at < kAlphaMax ? dLda : 0.f;
+              v[8] = G * d_at;
+              const float w = at * d_at;
+              v[0] = w * (2.f * a.z * dx + a.w * dy);
+              v[1] = w * (a.w * dx + 2.f * b.x * dy);
+              v[2] = w * dx * dx;
+              v[3] = w * dx * dy;
+              v[4] = w * dy * dy;
+            }
           }
         }
         float* gdst = g2d + (size_t)s_rank[j] * 12;
@@ -253,46 +272,47 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
           }
         } else {
           const uint32_t active = __ballot_sync(0xffffffffu, frag);
+          const bool reduce = active != 0u && __popc(active) >= threshold;
           float tot = 0.f;
-          if (active != 0u) {
-            if (__popc(active) < threshold) {   // few lanes: add directly (Sec. 3.2.3)
-              if (frag) {
-                red_add_v4(gdst, v[0], v[1], v[2], v[3]);
-                red_add_v4(gdst + 4, v[4], v[5], v[6], v[7]);
-                red_add_v4(gdst + 8, v[8], 0.f, 0.f, 0.f);
-              }
-            } else {
-              tot = warp_transpose_reduce9(v, lane);
+          if (active != 0u && !reduce) {    // few lanes: add directly (Sec. 3.2.3)
+            if (frag) {
+              red_add_v4(gdst, v[0], v[1], v[2], v[3]);
+              red_add_v4(gdst + 4, v[4], v[5], v[6], v[7]);
+              red_add_v4(gdst + 8, v[8], 0.f, 0.f, 0.f);
             }
+          } else if (reduce) {
+            tot = warp_transpose_reduce9(v, lane);
           }
-          if (slot >= 0) s_part[jj][warp][slot] = (active != 0u && __popc(active) >= threshold) ? tot : 0.f;
+          if (slot >= 0) s_part[jj][warp][slot] = tot;
         }
       }
       if (MODE != GS_REDUCE_NAIVE) {
         __syncthreads();
         if (MODE == GS_REDUCE_BLOCK) {
-          // one thread per (splat, float4 group): sum the eight warps
-          if (tid < kSub * 3) {
+          // one thread per (splat, float4 group): sum the warps that looked at it
+          if (tid < 32 * 3) {
             const int jj = tid / 3, q = tid % 3;
-            if (jj < jn) {
+            if (k * 32 + jj < cnt) {
               float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-              for (int w = 0; w < kBlockPixels / 32; ++w) {
-                const float4 p = *reinterpret_cast<const float4*>(&s_part[jj][w][4 * q]);
-                acc.x += p.x; acc.y += p.y; acc.z += p.z; acc.w += p.w;
+              for (int w = 0; w < kWarps; ++w) {
+                if ((s_mask[w] >> jj) & 1u) {
+                  const float4 p = *reinterpret_cast<const float4*>(&s_part[jj][w][4 * q]);
+                  acc.x += p.x; acc.y += p.y; acc.z += p.z; acc.w += p.w;
+                }
               }
               if (acc.x != 0.f || acc.y != 0.f || acc.z != 0.f || acc.w != 0.f)
-                red_add_v4(g2d + (size_t)s_rank[j0 + jj] * 12 + 4 * q, acc.x, acc.y, acc.z, acc.w);
+                red_add_v4(g2d + (size_t)s_rank[k * 32 + jj] * 12 + 4 * q, acc.x, acc.y, acc.z, acc.w);
             }
           }
         } else {
           // GS_REDUCE_WARP: each warp adds its own partial sums
-          if (lane < jn) {
+          if ((s_mask[warp] >> lane) & 1u) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               const float4 p = *reinterpret_cast<const float4*>(&s_part[lane][warp][4 * q]);
               if (p.x != 0.f || p.y != 0.f || p.z != 0.f || p.w != 0.f)
-                red_add_v4(g2d + (size_t)s_rank[j0 + lane] * 12 + 4 * q, p.x, p.y, p.z, p.w);
+                red_add_v4(g2d + (size_t)s_rank[k * 32 + lane] * 12 + 4 * q, p.x, p.y, p.z, p.w);
             }
           }
         }

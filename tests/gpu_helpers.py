@@ -12,8 +12,18 @@ AMBIG_IMAGE = 1 | 2 | 4 | 8
 GROUPS = ("means", "scales", "quats", "opacities", "sh")
 
 
-def oracle_opts(opts: gs.RasterOpts, **kw):
+def cut_band(cam) -> float:
+    """Tie band on |power - ln(1/(255 o))| for this image size.  The FP32 centre
+    mu_2D carries ~2e-7 * (image size) px of rounding error, which moves power by
+    up to ~3/sigma times that (sigma >= 0.55 px after the 0.3 dilation); the band
+    is about 5x that bound, and never below 5e-4."""
+    return max(5e-4, 3e-6 * max(int(cam.width), int(cam.height)))
+
+
+def oracle_opts(opts: gs.RasterOpts, cam=None, **kw):
     clamp = opts.state_format in ("unorm16", "unorm8")
+    if cam is not None and "band_cut" not in kw:
+        kw["band_cut"] = cut_band(cam)
     return oracle.opts_array(t_cull=opts.t_cull, clamp01=clamp, **kw)
 
 

@@ -116,7 +116,7 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     ids = gs.copy_array(ws, gs._lib.GS_ARRAY_SORTED_IDS, V).cpu().numpy()
     rec = gs.copy_array(ws, gs._lib.GS_ARRAY_RECORDS, scene.n).cpu().numpy()[ids]
     f = np.float32
-    ux, uy, ex, ey = rec[:, 0], rec[:, 1], rec[:, 7], rec[:, 11]
+    ux, uy, ex, ey = rec[:, 0], rec[:, 1], rec[:, 11], rec[:, 7]
     x0 = np.maximum(np.ceil(ux - ex - f(0.5)), 0).astype(np.int64)
     x1 = np.minimum(np.floor(ux + ex - f(0.5)), cam.width - 1).astype(np.int64)
     y0 = np.maximum(np.ceil(uy - ey - f(0.5)), 0).astype(np.int64)
@@ -130,9 +130,9 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
 # Forward
 # ---------------------------------------------------------------------------
 
-def _check_forward(scene_np, cam, opts, max_ambig_frac=0.1):
+def _check_forward(scene_np, cam, opts, max_ambig_frac=0.2):
     scene, ws, out = run_forward(scene_np, cam, opts)
-    ref = oracle.render(scene_np, cam, oracle_opts(opts))
+    ref = oracle.render(scene_np, cam, oracle_opts(opts, cam))
     ok = (ref["ambig"] & AMBIG_IMAGE) == 0
     assert ok.mean() >= 1.0 - max_ambig_frac, f"too many tie-band pixels: {1 - ok.mean():.3f}"
     img = out["image"].cpu().numpy().astype(np.float64)
@@ -232,7 +232,7 @@ def test_invalid_arguments_are_rejected():
 
 def _check_backward(scene_np, cam, opts, g, tol=1e-3):
     scene, ws, out, grads = run_forward_backward(scene_np, cam, opts, g)
-    ref = oracle.backward(scene_np, cam, g.astype(np.float64), oracle_opts(opts))
+    ref = oracle.backward(scene_np, cam, g.astype(np.float64), oracle_opts(opts, cam))
     errs = {k: rel_l2(grads[k], ref[k]) for k in GROUPS}
     for k, e in errs.items():
         assert e <= tol, f"{k}: rel-L2 {e:.3e} ({errs})"
@@ -254,9 +254,9 @@ def test_backward_tiny_scene_l2_loss_path():
     dl, loss = gs.loss(out["image"], tt, "l2")
     grads = gs.raster_backward(ws, scene, cam, opts, out["state"], out["last"], dl)
     torch.cuda.synchronize()
-    img_ref = oracle.render(scene_np, cam, oracle_opts(opts))["color"]
+    img_ref = oracle.render(scene_np, cam, oracle_opts(opts, cam))["color"]
     g_ref = 2.0 * (img_ref - target.astype(np.float64))
-    ref = oracle.backward(scene_np, cam, g_ref, oracle_opts(opts))
+    ref = oracle.backward(scene_np, cam, g_ref, oracle_opts(opts, cam))
     assert abs(loss.item() - np.sum((img_ref - target) ** 2)) / np.sum((img_ref - target) ** 2) < 1e-5
     for k in GROUPS:
         assert rel_l2(grads[k].cpu().numpy().astype(np.float64), ref[k]) <= 1e-3, k
@@ -308,7 +308,7 @@ def test_gradients_accumulate_over_views():
         g = syn.uniform_image(cam.height, cam.width, seed=70 + i, lo=-1.0, hi=1.0)
         out = gs.render(ws, scene, cam, opts)
         gs.raster_backward(ws, scene, cam, opts, out["state"], out["last"], torch.from_numpy(g).cuda(), grads)
-        ref = oracle.backward(scene_np, cam, g.astype(np.float64), oracle_opts(opts))
+        ref = oracle.backward(scene_np, cam, g.astype(np.float64), oracle_opts(opts, cam))
         for k in GROUPS:
             gsum[k] = gsum[k] + ref[k]
     torch.cuda.synchronize()
@@ -368,7 +368,7 @@ def test_reduced_precision_state(fmt, img_tol, grad_tol):
     for i, cam in enumerate(cams):
         g = syn.uniform_image(cam.height, cam.width, seed=90 + i, lo=-1.0, hi=1.0)
         scene, ws, out, grads = run_forward_backward(scene_np, cam, opts, g)
-        oo = oracle_opts(opts)
+        oo = oracle_opts(opts, cam)
         ref_img = oracle.render(scene_np, cam, oo)
         ok = (ref_img["ambig"] & AMBIG_IMAGE) == 0
         st = gs.decode_state(out["state"], fmt).cpu().numpy().astype(np.float64)
