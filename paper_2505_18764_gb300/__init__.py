@@ -320,7 +320,7 @@ _ARRAY_DTYPES = {
     _lib.GS_ARRAY_SORTED_IDS: (torch.int32, 1), _lib.GS_ARRAY_DEPTH_KEYS: (torch.int32, 1),
     _lib.GS_ARRAY_RECORDS: (torch.float32, 12), _lib.GS_ARRAY_PAIR_BLOCKS: (torch.int32, 1),
     _lib.GS_ARRAY_PAIR_RANKS: (torch.int32, 1), _lib.GS_ARRAY_RANGES: (torch.int32, 2),
-    _lib.GS_ARRAY_GRAD2D: (torch.float32, 12),
+    _lib.GS_ARRAY_GRAD2D: (torch.float32, 12), _lib.GS_ARRAY_BOXES: (torch.int32, 2),
 }
 
 

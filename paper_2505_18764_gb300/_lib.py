@@ -25,7 +25,7 @@ GS_REDUCE_BLOCK, GS_REDUCE_WARP, GS_REDUCE_NAIVE = 0, 1, 2
 GS_MODE_FORWARD, GS_MODE_FORWARD_BACKWARD = 0, 1
 GS_LOSS_NONE, GS_LOSS_L1, GS_LOSS_L2 = 0, 1, 2
 (GS_ARRAY_SORTED_IDS, GS_ARRAY_DEPTH_KEYS, GS_ARRAY_RECORDS, GS_ARRAY_PAIR_BLOCKS,
- GS_ARRAY_PAIR_RANKS, GS_ARRAY_RANGES, GS_ARRAY_GRAD2D) = range(7)
+ GS_ARRAY_PAIR_RANKS, GS_ARRAY_RANGES, GS_ARRAY_GRAD2D, GS_ARRAY_BOXES) = range(8)
 
 
 class GsCamera(Structure):

@@ -12,8 +12,8 @@ namespace gsr {
 // launchers (kernels live in the other translation units)
 struct CamDev;
 cudaError_t launch_project_fwd(const float*, const float*, const float*, const float*, const float*,
-                               int, int, const gs_camera&, int, SplatRec*, uint32_t*, Header*,
-                               uint2*, int, uint32_t*, int, cudaStream_t);
+                               int, int, const gs_camera&, int, SplatRec*, uint2*, uint32_t*,
+                               Header*, uint2*, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_project_bwd(const float*, const float*, const float*, const float*, const float*,
                                int, int, const gs_camera&, int, const uint32_t*, const float*,
                                const Header*, float*, float*, float*, float*, float*, int,
@@ -24,9 +24,9 @@ cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, ui
                                  uint32_t, uint32_t*, int, int, cudaStream_t);
 cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
-cudaError_t launch_bin(const uint32_t*, const SplatRec*, SplatRec*, float*, Header*,
+cudaError_t launch_bin(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*, Header*,
                        unsigned long long*, const uint32_t*, uint32_t*, uint2*, uint32_t*, uint32_t*,
-                       uint32_t*, uint32_t, int, int, int, int, int, int, cudaStream_t);
+                       uint32_t*, uint32_t, int, int, int, int, cudaStream_t);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, cudaStream_t);
 cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const SplatRec*, int, int, int, int,
                               float, int, float*, void*, uint32_t*, uint32_t*, cudaStream_t);
@@ -88,6 +88,7 @@ enum Slot {
   L_KEYS,        // [n] depth keys (0xFFFFFFFF = culled)
   L_KA, L_VA, L_KB, L_VB,   // [n] sort ping-pong
   L_REC,         // [n] records by splat id
+  L_BOXES_ID,    // [n] uint2 16x16-block box of each splat, by splat id
   L_REC_SORTED,  // [n] records by depth rank
   L_G2D,         // [n][12] backward accumulators by depth rank
   L_OFFSETS,     // [n] first pair index of each depth rank
@@ -126,6 +127,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_KA] = sz[L_VA] = sz[L_KB] = sz[L_VB] = n_cap * 4;
   sz[L_REC] = sz[L_REC_SORTED] = sz[L_G2D] = n_cap * sizeof(SplatRec);
   sz[L_OFFSETS] = n_cap * 4;
+  sz[L_BOXES_ID] = n_cap * 8;
   sz[L_BOXES] = n_cap * 8;
   sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
@@ -256,7 +258,8 @@ int gs_project(gs_workspace* ws, const float* means, const float* scales, const 
   ws->pair_passes = pair_passes_for(blocks);
   GS_CUDA(cudaMemsetAsync(at<Header>(ws, L_HDR), 0, sizeof(Header), st), "gs_project memset");
   GS_CUDA(launch_project_fwd(means, scales, quats, opacities, sh, n, opts->sh_degree, *cam,
-                             ws->clamp01, at<SplatRec>(ws, L_REC), at<uint32_t>(ws, L_KEYS),
+                             ws->clamp01, at<SplatRec>(ws, L_REC), at<uint2>(ws, L_BOXES_ID),
+                             at<uint32_t>(ws, L_KEYS),
                              at<Header>(ws, L_HDR), at<uint2>(ws, L_RANGES), blocks,
                              at<uint32_t>(ws, L_EPOCH), num_sms(), st),
           "project kernel");
@@ -309,11 +312,12 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int grid_cap = num_sms() * kPersistentPerSm;
-  GS_CUDA(launch_bin(at<uint32_t>(ws, L_VB), at<SplatRec>(ws, L_REC), at<SplatRec>(ws, L_REC_SORTED),
+  GS_CUDA(launch_bin(at<uint32_t>(ws, L_VB), at<SplatRec>(ws, L_REC), at<uint2>(ws, L_BOXES_ID),
+                     at<SplatRec>(ws, L_REC_SORTED),
                      at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN), epoch,
                      at<uint32_t>(ws, L_OFFSETS), at<uint2>(ws, L_BOXES), at<uint32_t>(ws, L_CHUNKS),
                      at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PVA), (uint32_t)ws->pair_cap,
-                     cam->width, cam->height, gw, ws->pair_passes, ws->n, grid_cap, st),
+                     gw, ws->pair_passes, ws->n, grid_cap, st),
           "bin kernel");
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
   uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};
@@ -508,6 +512,7 @@ int gs_copy_array(gs_workspace* ws, int32_t which, void* dst, size_t bytes, gs_s
     case GS_ARRAY_PAIR_RANKS: slot = fin ? L_PVB : L_PVA; cap = (size_t)ws->pair_cap * 4; break;
     case GS_ARRAY_RANGES: slot = L_RANGES; cap = (size_t)blocks_of(ws->width_cap, ws->height_cap, gw, gh) * 8; break;
     case GS_ARRAY_GRAD2D: slot = L_G2D; cap = (size_t)ws->n_cap * 48; break;
+    case GS_ARRAY_BOXES: slot = L_BOXES; cap = (size_t)ws->n_cap * 8; break;
     default: return fail(GS_ERR_INVALID_ARG, "unknown array %d", which);
   }
   if (bytes > cap) return fail(GS_ERR_INVALID_ARG, "asked for %zu bytes, array holds %zu", bytes, cap);

@@ -28,26 +28,14 @@ constexpr unsigned long long kBinPre = 2ull << 30;
 constexpr unsigned long long kBinCount = (1ull << 30) - 1;
 constexpr int kEmitChunk = 2048;  // pairs written per CTA step of the emission pass
 
-// Pixel-centre box of a record, clamped to the image, in block units.
-__device__ __forceinline__ bool record_blocks(const SplatRec& r, int W, int H, int& bx0, int& by0,
-                                              int& bx1, int& by1) {
-  const float ux = r.a.x, uy = r.a.y, ex = r.c.w, ey = r.b.w;
-  const float fx0 = ceilf(ux - ex - 0.5f), fx1 = floorf(ux + ex - 0.5f);
-  const float fy0 = ceilf(uy - ey - 0.5f), fy1 = floorf(uy + ey - 0.5f);
-  const int x0 = (int)fmaxf(fx0, 0.f), x1 = (int)fminf(fx1, (float)(W - 1));
-  const int y0 = (int)fmaxf(fy0, 0.f), y1 = (int)fminf(fy1, (float)(H - 1));
-  if (!(fx0 <= fx1) || !(fy0 <= fy1) || x0 > x1 || y0 > y1) return false;
-  bx0 = x0 >> 4; bx1 = x1 >> 4; by0 = y0 >> 4; by1 = y1 >> 4;
-  return true;
-}
-
 // Pass 1: one tile of 1024 depth ranks per step of a persistent loop.
 __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
     const uint32_t* __restrict__ sorted_ids, const SplatRec* __restrict__ rec,
-    SplatRec* __restrict__ rec_sorted, float4* __restrict__ g2d, Header* __restrict__ hdr,
+    const uint2* __restrict__ boxes_by_id, SplatRec* __restrict__ rec_sorted,
+    float4* __restrict__ g2d, Header* __restrict__ hdr,
     unsigned long long* __restrict__ scan_status, const uint32_t* __restrict__ epoch,
     uint32_t* __restrict__ offsets, uint2* __restrict__ boxes, uint32_t* __restrict__ chunk_rank,
-    uint32_t pair_cap, int W, int H) {
+    uint32_t pair_cap) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_cnt[kBinTile];
   __shared__ uint32_t s_warp[kBinThreads / 32];
@@ -70,20 +58,15 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
       const uint32_t r = base + j;
       uint32_t cnt = 0;
       if (r < V) {
-        const SplatRec R = rec[sorted_ids[r]];
-        rec_sorted[r] = R;
+        const uint32_t id = sorted_ids[r];
+        rec_sorted[r] = rec[id];
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         g2d[3 * (size_t)r] = z;
         g2d[3 * (size_t)r + 1] = z;
         g2d[3 * (size_t)r + 2] = z;
-        int bx0, by0, bx1, by1;
-        uint2 box = make_uint2(0u, 0u);
-        if (record_blocks(R, W, H, bx0, by0, bx1, by1)) {
-          const uint32_t w = bx1 - bx0 + 1, h = by1 - by0 + 1;
-          cnt = w * h;
-          box = make_uint2((uint32_t)bx0 | ((uint32_t)by0 << 16), w | (h << 16));
-        }
+        const uint2 box = boxes_by_id[id];   // every visible splat covers >= 1 block
         boxes[r] = box;
+        cnt = (box.y & 0xFFFFu) * (box.y >> 16);
       }
       s_cnt[j] = cnt;
     }
@@ -230,18 +213,18 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
   }
 }
 
-cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, SplatRec* rec_sorted,
-                       float* g2d, Header* hdr, unsigned long long* scan_status,
-                       const uint32_t* epoch, uint32_t* offsets, uint2* boxes,
-                       uint32_t* chunk_rank, uint32_t* pair_keys, uint32_t* pair_vals,
-                       uint32_t pair_cap, int W, int H, int gw, int pair_passes, int n_cap,
+cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, const uint2* boxes_by_id,
+                       SplatRec* rec_sorted, float* g2d, Header* hdr,
+                       unsigned long long* scan_status, const uint32_t* epoch, uint32_t* offsets,
+                       uint2* boxes, uint32_t* chunk_rank, uint32_t* pair_keys,
+                       uint32_t* pair_vals, uint32_t pair_cap, int gw, int pair_passes, int n_cap,
                        int grid_cap, cudaStream_t st) {
   int tiles = (n_cap + kBinTile - 1) / kBinTile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > grid_cap) tiles = grid_cap;
-  bin_count_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, rec_sorted,
+  bin_count_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, boxes_by_id, rec_sorted,
                                                   reinterpret_cast<float4*>(g2d), hdr, scan_status,
-                                                  epoch, offsets, boxes, chunk_rank, pair_cap, W, H);
+                                                  epoch, offsets, boxes, chunk_rank, pair_cap);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int chunks = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);

@@ -40,10 +40,13 @@ struct Header {
 };
 
 // Projected splat record, 48 B (three float4):
-//   a = (mu_x, mu_y, A, B), b = (C, thr, o, ext_y), c = (r, g, b, ext_x)
+//   a = (mu_x, mu_y, A, B), b = (C, thr, mu_x_lo, mu_y_lo), c = (r, g, b, o)
 // with power2 = A dx^2 + B dx dy + C dy^2 = log2(e) * power, i.e.
 // (A, B, C) = -log2(e) * (a/2, b, c/2) of the conic [[a, b], [b, c]], and
 // thr = log2(1 / (255 o)): a fragment exists iff power2 >= thr (alpha >= 1/255).
+// The screen centre is a float-float pair mu + mu_lo: at 1000-pixel
+// coordinates one FP32 ulp is 6e-5 px, which over a hundred fragments moves a
+// pixel's colour by ~1e-4; the pair keeps dx, dy exact to FP32 rounding of dx.
 struct __align__(16) SplatRec {
   float4 a, b, c;
 };
@@ -60,12 +63,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // here uses explicitly rounded intrinsics, which the compiler never contracts
 // or reorders.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float frag_power2(float px, float py, const float4& a, float C,
+__device__ __forceinline__ float frag_power2(float px, float py, const float4& a, const float4& b,
                                              float& dx, float& dy) {
-  dx = __fsub_rn(px, a.x);
-  dy = __fsub_rn(py, a.y);
+  dx = __fsub_rn(__fsub_rn(px, a.x), b.z);
+  dy = __fsub_rn(__fsub_rn(py, a.y), b.w);
   const float t = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));   // A dx + B dy
-  const float u = __fmul_rn(__fmul_rn(C, dy), dy);          // C dy^2
+  const float u = __fmul_rn(__fmul_rn(b.x, dy), dy);        // C dy^2
   return __fmaf_rn(dx, t, u);
 }
 
@@ -86,18 +89,67 @@ __device__ __forceinline__ float next_T(float T, float alpha) {
 // rounding of frag_power2 (it only decides what to skip).
 __device__ __forceinline__ bool strip_may_hit(const float4& a, const float4& b, float xs,
                                               float ys) {
-  const float X0 = xs - a.x, X1 = X0 + 15.0f;
+  const float X0 = (xs - a.x) - b.z, X1 = X0 + 15.0f;
   const float slope = -0.5f * a.w * __frcp_rn(a.z);  // vertex dx = slope * dy (A < 0)
   const float lim = b.y - 0.01f - 1e-3f * fabsf(b.y);
   bool hit = false;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const float Y = ys + (float)r - a.y;
+    const float Y = (ys + (float)r - a.y) - b.w;
     const float dx = fminf(fmaxf(slope * Y, X0), X1);
     const float f = (a.z * dx + a.w * Y) * dx + b.x * Y * Y;
     hit |= f >= lim;
   }
   return hit;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float ("double-float") arithmetic from error-free transformations
+// (Knuth's two-sum, FMA-based two-product); used once per splat to place the
+// screen centre to ~1e-12 relative without FP64.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ FF ff_norm(float hi, float lo) {  // |hi| >= |lo|
+  const float s = __fadd_rn(hi, lo);
+  return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ FF ff_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  return ff_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_add_f(FF x, float b) {
+  const FF s = ff_two_sum(x.hi, b);
+  return ff_norm(s.hi, __fadd_rn(s.lo, x.lo));
+}
+__device__ __forceinline__ FF ff_mul_f(FF x, float b) {
+  const FF p = ff_two_prod(x.hi, b);
+  return ff_norm(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+__device__ __forceinline__ FF ff_div(FF x, FF y) {
+  const float q1 = __fdiv_rn(x.hi, y.hi);
+  const FF qy = ff_mul_f(y, q1);
+  const FF r = ff_add(x, FF{-qy.hi, -qy.lo});
+  return ff_norm(q1, __fdiv_rn(r.hi, y.hi));
+}
+// sum_j a_j b_j + c, compensated
+__device__ __forceinline__ FF ff_dot3_add(const float* a, float b0, float b1, float b2, float c) {
+  FF s = ff_two_prod(a[0], b0);
+  s = ff_add(s, ff_two_prod(a[1], b1));
+  s = ff_add(s, ff_two_prod(a[2], b2));
+  return ff_add_f(s, c);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,7 +4,8 @@
 // Sigma_3D = R S S^T R^T; Sigma_2D = J W Sigma_3D W^T J^T + 0.3 I;
 // conic = Sigma_2D^-1; mu_2D = (fx tx/tz + cx, fy ty/tz + cy); SH colour; the
 // alpha >= 1/255 ellipse's bounding box (the screen quad the paper rasterizes)
-// and an off-screen / opacity-floor cull.  Writes the 48-B record, the depth
+// and an off-screen / opacity-floor cull.  Writes the 48-B record, the box's
+// 16x16 pixel blocks, the depth
 // key (FP32 bits of tz, or 0xFFFFFFFF when culled), the visible count and the
 // four 8-bit digit histograms the depth sort needs.
 //
@@ -106,8 +107,9 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float4* __restrict__ quats, const float* __restrict__ opac,
     const float* __restrict__ sh, int n, int deg, CamDev cam, int clamp01,
-    SplatRec* __restrict__ rec, uint32_t* __restrict__ keys, Header* __restrict__ hdr,
-    uint2* __restrict__ ranges, int n_ranges, uint32_t* __restrict__ epoch) {
+    SplatRec* __restrict__ rec, uint2* __restrict__ boxes, uint32_t* __restrict__ keys,
+    Header* __restrict__ hdr, uint2* __restrict__ ranges, int n_ranges,
+    uint32_t* __restrict__ epoch) {
   __shared__ uint32_t s_hist[4][256];
   // a new view: look-back status words of earlier views stop matching
   if (blockIdx.x == 0 && threadIdx.x == 0) *epoch += 1u;
@@ -134,9 +136,13 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     if (ok) {
       const float idet = 1.f / det;
       const float ca = ps.s2[2] * idet, cb = -ps.s2[1] * idet, cc = ps.s2[0] * idet;
-      const float iz = 1.f / ps.t[2];
-      const float ux = cam.fx * ps.t[0] * iz + cam.cx;
-      const float uy = cam.fy * ps.t[1] * iz + cam.cy;
+      // screen centre in float-float: t = W mu + w and mu_2D = f t_xy / t_z + c
+      const FF tx = ff_dot3_add(&cam.R[0], mx, my, mz, cam.t[0]);
+      const FF ty = ff_dot3_add(&cam.R[3], mx, my, mz, cam.t[1]);
+      const FF tz = ff_dot3_add(&cam.R[6], mx, my, mz, cam.t[2]);
+      const FF fux = ff_add_f(ff_mul_f(ff_div(tx, tz), cam.fx), cam.cx);
+      const FF fuy = ff_add_f(ff_mul_f(ff_div(ty, tz), cam.fy), cam.cy);
+      const float ux = fux.hi, uy = fuy.hi;
       // power >= -ln(255 o)  <=>  d^T Q d <= k = 2 ln(255 o); the ellipse's box
       // has half-widths sqrt(k Sigma_00), sqrt(k Sigma_11).  A small relative
       // and absolute widening keeps every fragment the FP32 raster accepts.
@@ -150,6 +156,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
       ok = x0 <= x1 && y0 <= y1 && x1 >= 0.f && y1 >= 0.f && x0 <= (float)(cam.W - 1) &&
            y0 <= (float)(cam.H - 1);
       if (ok) {
+        // 16x16 blocks of the pixel-centre box (clamped to the image)
+        const int bx0 = (int)fmaxf(x0, 0.f) >> 4, bx1 = (int)fminf(x1, (float)(cam.W - 1)) >> 4;
+        const int by0 = (int)fmaxf(y0, 0.f) >> 4, by1 = (int)fminf(y1, (float)(cam.H - 1)) >> 4;
+        boxes[i] = make_uint2((uint32_t)bx0 | ((uint32_t)by0 << 16),
+                              (uint32_t)(bx1 - bx0 + 1) | ((uint32_t)(by1 - by0 + 1) << 16));
         // colour from SH at the view direction
         float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
         const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
@@ -170,8 +181,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         }
         SplatRec r;
         r.a = make_float4(ux, uy, -0.5f * kLog2e * ca, -kLog2e * cb);
-        r.b = make_float4(-0.5f * kLog2e * cc, thr, o, ey);
-        r.c = make_float4(col[0], col[1], col[2], ex);
+        r.b = make_float4(-0.5f * kLog2e * cc, thr, fux.lo, fuy.lo);
+        r.c = make_float4(col[0], col[1], col[2], o);
         rec[i] = r;
         key = __float_as_uint(ps.t[2]);
         local_visible++;
@@ -387,16 +398,16 @@ CamDev make_cam(const gs_camera& c) {
 
 cudaError_t launch_project_fwd(const float* means, const float* scales, const float* quats,
                                const float* opac, const float* sh, int n, int deg,
-                               const gs_camera& cam, int clamp01, SplatRec* rec, uint32_t* keys,
-                               Header* hdr, uint2* ranges, int n_ranges, uint32_t* epoch,
-                               int num_sms, cudaStream_t st) {
+                               const gs_camera& cam, int clamp01, SplatRec* rec, uint2* boxes,
+                               uint32_t* keys, Header* hdr, uint2* ranges, int n_ranges,
+                               uint32_t* epoch, int num_sms, cudaStream_t st) {
   int blocks = (n + 255) / 256;
   const int cap = num_sms * 8;  // persistent: a few waves' worth of CTAs
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   project_fwd_kernel<<<blocks, 256, 0, st>>>(means, scales, reinterpret_cast<const float4*>(quats),
-                                             opac, sh, n, deg, make_cam(cam), clamp01, rec, keys,
-                                             hdr, ranges, n_ranges, epoch);
+                                             opac, sh, n, deg, make_cam(cam), clamp01, rec, boxes,
+                                             keys, hdr, ranges, n_ranges, epoch);
   return cudaGetLastError();
 }
 

@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(kBlockPixels) raster_fwd_kernel(
         const float4 a = s_a[j];
         const float4 b = s_b[j];
         float dx, dy;
-        const float p2 = frag_power2(px, py, a, b.x, dx, dy);
+        const float p2 = frag_power2(px, py, a, b, dx, dy);
         if (p2 < b.y) continue;            // alpha < 1/255
-        float G, at;
-        const float alpha = frag_alpha(b.z, p2, G, at);
         const float4 c = s_c[j];
+        float G, at;
+        const float alpha = frag_alpha(c.w, p2, G, at);
         const float w = __fmul_rn(alpha, T);
         C0 = __fmaf_rn(w, c.x, C0);
         C1 = __fmaf_rn(w, c.y, C1);
@@ -230,12 +230,12 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
             const float4 a = s_a[j];
             const float4 b = s_b[j];
             float dx, dy;
-            const float p2 = frag_power2(px, py, a, b.x, dx, dy);
+            const float p2 = frag_power2(px, py, a, b, dx, dy);
             if (p2 >= b.y) {
               frag = true;
-              float G, at;
-              const float alpha = frag_alpha(b.z, p2, G, at);
               const float4 c = s_c[j];
+              float G, at;
+              const float alpha = frag_alpha(c.w, p2, G, at);
               const float oma = __fsub_rn(1.0f, alpha);
               const float wT = __fmul_rn(alpha, T);
               // Eq. 3

@@ -45,7 +45,8 @@ def test_projection_records_match_oracle():
     vis = keys != 0xFFFFFFFF
     assert vis.sum() > 500
     assert np.all(P[vis, 0] == 1.0)
-    np.testing.assert_allclose(rec[vis, 0:2], P[vis, 1:3], rtol=0, atol=2e-4)
+    # float-float screen centre (hi + lo) against the FP64 projection
+    np.testing.assert_allclose(rec[vis, 0:2] + rec[vis, 6:8], P[vis, 1:3], rtol=0, atol=2e-6)
     a = rec[vis, 2] / (-0.5 * LOG2E)
     b = rec[vis, 3] / (-LOG2E)
     c = rec[vis, 4] / (-0.5 * LOG2E)
@@ -53,6 +54,7 @@ def test_projection_records_match_oracle():
     np.testing.assert_allclose(rec[vis, 8:11], P[vis, 9:12], rtol=0, atol=2e-5)
     o = scene_np.opacities.astype(np.float64)
     np.testing.assert_allclose(rec[vis, 5], np.log2(1.0 / (255.0 * o[vis])), rtol=1e-5, atol=1e-5)
+    np.testing.assert_array_equal(rec[vis, 11], o[vis].astype(np.float32))
     np.testing.assert_allclose(keys[vis].view(np.float32), P[vis, 12], rtol=1e-6)
     # every splat the GPU culled has no pixel centre inside its alpha >= 1/255 box
     cull = ~vis & (P[:, 0] == 1.0) & (o * 255.0 > 1.0)
@@ -112,18 +114,26 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     for b in np.unique(blocks):
         s, e = ranges[b]
         assert np.all(blocks[s:e] == b) and (s == 0 or blocks[s - 1] != b) and (e == P or blocks[e] != b)
-    # each splat's pairs = the blocks of its pixel-centre box (recomputed in float32 here)
+    # each splat's pairs are exactly the blocks of its box, and every box holds
+    # the blocks the oracle's alpha >= 1/255 ellipse reaches
+    boxes = gs.copy_array(ws, gs._lib.GS_ARRAY_BOXES, V).cpu().numpy().astype(np.int64)
+    bx0, by0 = boxes[:, 0] & 0xFFFF, boxes[:, 0] >> 16
+    w, h = boxes[:, 1] & 0xFFFF, boxes[:, 1] >> 16
+    np.testing.assert_array_equal(np.bincount(ranks, minlength=V), w * h)
+    gw = (cam.width + 15) // 16
+    pbx, pby = blocks % gw, blocks // gw
+    assert np.all((pbx >= bx0[ranks]) & (pbx < bx0[ranks] + w[ranks]) &
+                  (pby >= by0[ranks]) & (pby < by0[ranks] + h[ranks]))
     ids = gs.copy_array(ws, gs._lib.GS_ARRAY_SORTED_IDS, V).cpu().numpy()
-    rec = gs.copy_array(ws, gs._lib.GS_ARRAY_RECORDS, scene.n).cpu().numpy()[ids]
-    f = np.float32
-    ux, uy, ex, ey = rec[:, 0], rec[:, 1], rec[:, 11], rec[:, 7]
-    x0 = np.maximum(np.ceil(ux - ex - f(0.5)), 0).astype(np.int64)
-    x1 = np.minimum(np.floor(ux + ex - f(0.5)), cam.width - 1).astype(np.int64)
-    y0 = np.maximum(np.ceil(uy - ey - f(0.5)), 0).astype(np.int64)
-    y1 = np.minimum(np.floor(uy + ey - f(0.5)), cam.height - 1).astype(np.int64)
-    want = np.where((x0 <= x1) & (y0 <= y1), ((x1 >> 4) - (x0 >> 4) + 1) * ((y1 >> 4) - (y0 >> 4) + 1), 0)
-    got = np.bincount(ranks, minlength=V)
-    np.testing.assert_array_equal(got, want)
+    Pj = oracle.project(scene_np, cam)[ids]
+    o = scene_np.opacities[ids].astype(np.float64)
+    k = 2.0 * np.log(255.0 * o)
+    ex, ey = np.sqrt(k * Pj[:, 3]), np.sqrt(k * Pj[:, 5])
+    x0 = np.clip(np.ceil(Pj[:, 1] - ex - 0.5), 0, cam.width - 1).astype(np.int64) >> 4
+    x1 = np.clip(np.floor(Pj[:, 1] + ex - 0.5), 0, cam.width - 1).astype(np.int64) >> 4
+    y0 = np.clip(np.ceil(Pj[:, 2] - ey - 0.5), 0, cam.height - 1).astype(np.int64) >> 4
+    y1 = np.clip(np.floor(Pj[:, 2] + ey - 0.5), 0, cam.height - 1).astype(np.int64) >> 4
+    assert np.all((bx0 <= x0) & (bx0 + w - 1 >= x1) & (by0 <= y0) & (by0 + h - 1 >= y1))
 
 
 # ---------------------------------------------------------------------------
