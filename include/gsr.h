@@ -237,9 +237,10 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
 
 /* Copies an internal array of `ws` into caller device memory `dst` (`bytes`):
  * GS_ARRAY_SORTED_IDS u32 [V], GS_ARRAY_DEPTH_KEYS u32 [n] (0xFFFFFFFF = culled),
- * GS_ARRAY_RECORDS float [n][12] (mu_x, mu_y, A, B, C, thr, mu_x_lo, mu_y_lo, r,
- * g, b, o with (A, B, C) = -log2(e) (a/2, b, c/2) of the conic, thr =
- * log2(1/(255 o)) and the screen centre mu + mu_lo as a float-float pair),
+ * GS_ARRAY_RECORDS float [n][12] (mu_x, mu_y, i11, k, i22, tau, mu_x_lo, mu_y_lo,
+ * r, g, b, o: the screen centre mu + mu_lo as a float-float pair, the inverse
+ * Cholesky factor of Sigma_2D scaled so that (i11 dx)^2 + (i22 (dy - k dx))^2 =
+ * -log2(e) * power, and tau = log2(255 o)),
  * GS_ARRAY_PAIR_BLOCKS u32 [P], GS_ARRAY_PAIR_RANKS u32 [P] (sorted by block),
  * GS_ARRAY_RANGES u32 [blocks][2], GS_ARRAY_GRAD2D float [V][12] (per depth
  * rank: the backward's unscaled accumulators), GS_ARRAY_BOXES u32 [V][2] (per

@@ -40,10 +40,14 @@ struct Header {
 };
 
 // Projected splat record, 48 B (three float4):
-//   a = (mu_x, mu_y, A, B), b = (C, thr, mu_x_lo, mu_y_lo), c = (r, g, b, o)
-// with power2 = A dx^2 + B dx dy + C dy^2 = log2(e) * power, i.e.
-// (A, B, C) = -log2(e) * (a/2, b, c/2) of the conic [[a, b], [b, c]], and
-// thr = log2(1 / (255 o)): a fragment exists iff power2 >= thr (alpha >= 1/255).
+//   a = (mu_x, mu_y, i11, k), b = (i22, tau, mu_x_lo, mu_y_lo), c = (r, g, b, o)
+// The Gaussian's exponent uses the inverse Cholesky factor of Sigma_2D:
+//   q = y1^2 + y2^2,  y1 = i11 dx,  y2 = i22 (dy - k dx),  q = -log2(e) * power,
+// i.e. k = s01 / s00, i11 = c / sqrt(s00), i22 = c sqrt(s00 / det) with
+// c = sqrt(log2(e) / 2).  Unlike the conic form a dx^2 + 2 b dx dy + c dy^2,
+// whose terms cancel along a needle's long axis (error ~ eigenvalue ratio x
+// FP32 epsilon), this form loses only ~ its square root.  tau = log2(255 o):
+// a fragment exists iff q <= tau (alpha >= 1/255).
 // The screen centre is a float-float pair mu + mu_lo: at 1000-pixel
 // coordinates one FP32 ulp is 6e-5 px, which over a hundred fragments moves a
 // pixel's colour by ~1e-4; the pair keeps dx, dy exact to FP32 rounding of dx.
@@ -63,17 +67,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // here uses explicitly rounded intrinsics, which the compiler never contracts
 // or reorders.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float frag_power2(float px, float py, const float4& a, const float4& b,
-                                             float& dx, float& dy) {
-  dx = __fsub_rn(__fsub_rn(px, a.x), b.z);
-  dy = __fsub_rn(__fsub_rn(py, a.y), b.w);
-  const float t = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));   // A dx + B dy
-  const float u = __fmul_rn(__fmul_rn(b.x, dy), dy);        // C dy^2
-  return __fmaf_rn(dx, t, u);
+__device__ __forceinline__ float frag_q(float px, float py, const float4& a, const float4& b,
+                                        float& y1, float& y2) {
+  const float dx = __fsub_rn(__fsub_rn(px, a.x), b.z);
+  const float dy = __fsub_rn(__fsub_rn(py, a.y), b.w);
+  y1 = __fmul_rn(a.z, dx);
+  y2 = __fmul_rn(b.x, __fmaf_rn(-a.w, dx, dy));
+  return __fmaf_rn(y1, y1, __fmul_rn(y2, y2));
 }
 
-__device__ __forceinline__ float frag_alpha(float opacity, float power2, float& G, float& at) {
-  G = ex2_approx(power2);
+__device__ __forceinline__ float frag_alpha(float opacity, float q, float& G, float& at) {
+  G = ex2_approx(-q);
   at = __fmul_rn(opacity, G);
   return fminf(kAlphaMax, at);
 }
@@ -84,21 +88,23 @@ __device__ __forceinline__ float next_T(float T, float alpha) {
 
 // Can any pixel centre of a warp's 16x2 strip hold a fragment of this splat?
 // The centres lie on two rows y = ys, ys + 1 and x in [xs, xs + 15]; along a
-// row, power2 is a concave quadratic in dx whose maximum over the segment is
-// at the clamped vertex.  The margin keeps the test conservative against the
-// rounding of frag_power2 (it only decides what to skip).
+// row, q is a convex quadratic in dx whose minimum over the segment is at the
+// clamped vertex.  The margin keeps the test conservative against the
+// rounding of frag_q (it only decides what to skip).
 __device__ __forceinline__ bool strip_may_hit(const float4& a, const float4& b, float xs,
                                               float ys) {
   const float X0 = (xs - a.x) - b.z, X1 = X0 + 15.0f;
-  const float slope = -0.5f * a.w * __frcp_rn(a.z);  // vertex dx = slope * dy (A < 0)
-  const float lim = b.y - 0.01f - 1e-3f * fabsf(b.y);
+  const float i11 = a.z, k = a.w, i22 = b.x;
+  const float ki = k * i22;
+  const float slope = ki * i22 * __frcp_rn(fmaf(i11, i11, ki * ki));  // vertex dx = slope * dy
+  const float lim = b.y + 0.01f + 1e-3f * b.y;
   bool hit = false;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const float Y = (ys + (float)r - a.y) - b.w;
     const float dx = fminf(fmaxf(slope * Y, X0), X1);
-    const float f = (a.z * dx + a.w * Y) * dx + b.x * Y * Y;
-    hit |= f >= lim;
+    const float y1 = i11 * dx, y2 = i22 * (Y - k * dx);
+    hit |= fmaf(y1, y1, y2 * y2) <= lim;
   }
   return hit;
 }

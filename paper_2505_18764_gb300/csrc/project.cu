@@ -37,23 +37,36 @@ __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, 
   R[8] = 1.f - 2.f * (x * x + y * y);
 }
 
-// Shared by forward and backward: everything up to Sigma_2D.
+// Shared by forward and backward: everything up to Sigma_2D.  Sigma_2D is
+// formed as N N^T + 0.3 I with N = J W R S (2x3) and its determinant as the
+// sum of the squared 2x2 minors of N (Cauchy-Binet) plus the dilation terms:
+// no step subtracts nearly equal numbers, so needle-shaped splats (eigenvalue
+// ratios of 1e4 and more) keep their short axis to FP32 precision.
 struct ProjState {
   float t[3];
   float qn[4], rq;       // normalised quaternion, 1/|q|
   float R[9];            // rotation
   float M[9];            // R diag(s)
-  float S3[6];           // Sigma_3D (xx, xy, xz, yy, yz, zz)
   float Tm[6];           // J W (2x3)
-  float s2[3];           // Sigma_2D (00, 01, 11)
+  float N[6];            // Tm M (2x3)
+  float s00, s01, s11;   // Sigma_2D
+  float det;             // det Sigma_2D
 };
+
+// a d - b c with one rounding (FMA-based, Kahan)
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+  const float w = b * c;
+  const float e = fmaf(-b, c, w);
+  const float f = fmaf(a, d, -w);
+  return f + e;
+}
 
 __device__ __forceinline__ bool project_core(const CamDev& cam, float mx, float my, float mz,
                                              float4 q, float sx, float sy, float sz,
                                              ProjState& ps) {
-  ps.t[0] = cam.R[0] * mx + cam.R[1] * my + cam.R[2] * mz + cam.t[0];
-  ps.t[1] = cam.R[3] * mx + cam.R[4] * my + cam.R[5] * mz + cam.t[1];
-  ps.t[2] = cam.R[6] * mx + cam.R[7] * my + cam.R[8] * mz + cam.t[2];
+  ps.t[0] = ff_dot3_add(&cam.R[0], mx, my, mz, cam.t[0]).hi;
+  ps.t[1] = ff_dot3_add(&cam.R[3], mx, my, mz, cam.t[1]).hi;
+  ps.t[2] = ff_dot3_add(&cam.R[6], mx, my, mz, cam.t[2]).hi;
   if (!(ps.t[2] > cam.znear)) return false;
   const float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
   if (!(qq > 0.f)) return false;
@@ -68,34 +81,30 @@ __device__ __forceinline__ bool project_core(const CamDev& cam, float mx, float 
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) ps.M[i * 3 + j] = ps.R[i * 3 + j] * s[j];
-  float S[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      S[i][j] = ps.M[i * 3 + 0] * ps.M[j * 3 + 0] + ps.M[i * 3 + 1] * ps.M[j * 3 + 1] +
-                ps.M[i * 3 + 2] * ps.M[j * 3 + 2];
-  ps.S3[0] = S[0][0]; ps.S3[1] = S[0][1]; ps.S3[2] = S[0][2];
-  ps.S3[3] = S[1][1]; ps.S3[4] = S[1][2]; ps.S3[5] = S[2][2];
   const float iz = 1.f / ps.t[2];
   const float J00 = cam.fx * iz, J02 = -cam.fx * ps.t[0] * iz * iz;
   const float J11 = cam.fy * iz, J12 = -cam.fy * ps.t[1] * iz * iz;
-  // Tm = J W
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
+  for (int j = 0; j < 3; ++j) {   // Tm = J W
     ps.Tm[j] = J00 * cam.R[j] + J02 * cam.R[6 + j];
     ps.Tm[3 + j] = J11 * cam.R[3 + j] + J12 * cam.R[6 + j];
   }
-  // Sigma_2D = Tm S Tm^T + 0.3 I
-  float TS[2][3];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-      TS[i][j] = ps.Tm[i * 3 + 0] * S[0][j] + ps.Tm[i * 3 + 1] * S[1][j] + ps.Tm[i * 3 + 2] * S[2][j];
-  ps.s2[0] = TS[0][0] * ps.Tm[0] + TS[0][1] * ps.Tm[1] + TS[0][2] * ps.Tm[2] + kDilation;
-  ps.s2[1] = TS[0][0] * ps.Tm[3] + TS[0][1] * ps.Tm[4] + TS[0][2] * ps.Tm[5];
-  ps.s2[2] = TS[1][0] * ps.Tm[3] + TS[1][1] * ps.Tm[4] + TS[1][2] * ps.Tm[5] + kDilation;
+    for (int j = 0; j < 3; ++j)    // N = Tm M
+      ps.N[i * 3 + j] = ps.Tm[i * 3 + 0] * ps.M[j] + ps.Tm[i * 3 + 1] * ps.M[3 + j] +
+                        ps.Tm[i * 3 + 2] * ps.M[6 + j];
+  const float* N = ps.N;
+  const float n0 = fmaf(N[0], N[0], fmaf(N[1], N[1], N[2] * N[2]));
+  const float n1 = fmaf(N[3], N[3], fmaf(N[4], N[4], N[5] * N[5]));
+  ps.s00 = n0 + kDilation;
+  ps.s11 = n1 + kDilation;
+  ps.s01 = fmaf(N[0], N[3], fmaf(N[1], N[4], N[2] * N[5]));
+  const float m01 = det2(N[0], N[1], N[3], N[4]);
+  const float m02 = det2(N[0], N[2], N[3], N[5]);
+  const float m12 = det2(N[1], N[2], N[4], N[5]);
+  ps.det = fmaf(m01, m01, fmaf(m02, m02, m12 * m12)) + kDilation * (n0 + n1) + kDilation * kDilation;
   return true;
 }
 
@@ -128,14 +137,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     bool ok = o * 255.0f >= 1.0f;   // opacity floor: alpha <= o < 1/255 everywhere
     if (ok) ok = project_core(cam, mx, my, mz, quats[i], scales[3 * i], scales[3 * i + 1],
                               scales[3 * i + 2], ps);
-    float det = 0.f;
+    if (ok) ok = ps.det > 0.f;
     if (ok) {
-      det = ps.s2[0] * ps.s2[2] - ps.s2[1] * ps.s2[1];
-      ok = det > 0.f;
-    }
-    if (ok) {
-      const float idet = 1.f / det;
-      const float ca = ps.s2[2] * idet, cb = -ps.s2[1] * idet, cc = ps.s2[0] * idet;
       // screen centre in float-float: t = W mu + w and mu_2D = f t_xy / t_z + c
       const FF tx = ff_dot3_add(&cam.R[0], mx, my, mz, cam.t[0]);
       const FF ty = ff_dot3_add(&cam.R[3], mx, my, mz, cam.t[1]);
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
       // and absolute widening keeps every fragment the FP32 raster accepts.
       const float thr = -log2f(255.0f * o);
       const float k = fmaxf(0.f, -2.0f * kLn2 * thr);
-      const float ex = sqrtf(k * ps.s2[0]) * 1.002f + 0.02f;
-      const float ey = sqrtf(k * ps.s2[2]) * 1.002f + 0.02f;
+      const float ex = sqrtf(k * ps.s00) * 1.002f + 0.02f;
+      const float ey = sqrtf(k * ps.s11) * 1.002f + 0.02f;
       // any pixel centre (x + 0.5, y + 0.5) inside the box?
       const float x0 = ceilf(ux - ex - 0.5f), x1 = floorf(ux + ex - 0.5f);
       const float y0 = ceilf(uy - ey - 0.5f), y1 = floorf(uy + ey - 0.5f);
@@ -179,9 +182,12 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
           col[c] = fmaxf(0.f, col[c]);
           if (clamp01) col[c] = fminf(1.f, col[c]);
         }
+        // inverse Cholesky factor of Sigma_2D, scaled so that
+        // q = (i11 dx)^2 + (i22 (dy - k dx))^2 = -log2(e) * power
+        const float sc = 0.84932180028801904f;   // sqrt(log2(e) / 2)
         SplatRec r;
-        r.a = make_float4(ux, uy, -0.5f * kLog2e * ca, -kLog2e * cb);
-        r.b = make_float4(-0.5f * kLog2e * cc, thr, fux.lo, fuy.lo);
+        r.a = make_float4(ux, uy, sc * rsqrtf(ps.s00), ps.s01 / ps.s00);
+        r.b = make_float4(sc * sqrtf(ps.s00 / ps.det), -thr, fux.lo, fuy.lo);
         r.c = make_float4(col[0], col[1], col[2], o);
         rec[i] = r;
         key = __float_as_uint(ps.t[2]);
@@ -207,9 +213,9 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
 
 // ---------------------------------------------------------------------------
 // Backward projection: one thread per visible depth rank.
-// g2 (12 floats per rank): U_x, U_y, S_xx, S_xy, S_yy, dr, dg, db, do, -, -, -
-// accumulated by the raster with the prescaled conic; converted here:
-//   dL/dmu_2D = -ln2 (U_x, U_y), dL/da = -S_xx / 2, dL/db = -S_xy, dL/dc = -S_yy / 2.
+// g2 (12 floats per rank): the raster's sums over fragments of w z_hat and
+// w z_hat z_hat^T (z_hat = Sigma_2D^-1 d / (2 ln 2), w = alpha_tilde dL/dalpha_tilde),
+// then dL/d(rgb) and dL/do; converted here to dL/dmu_2D and dL/dSigma_2D.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void project_bwd_one(
     const float* __restrict__ means, const float* __restrict__ scales,
@@ -227,12 +233,12 @@ __device__ __forceinline__ void project_bwd_one(
   const float sx = scales[3 * id], sy = scales[3 * id + 1], sz = scales[3 * id + 2];
   ProjState ps;
   project_core(cam, mx, my, mz, quats[id], sx, sy, sz, ps);
-  const float det = ps.s2[0] * ps.s2[2] - ps.s2[1] * ps.s2[1];
-  const float idet = 1.f / det;
-  const float qa = ps.s2[2] * idet, qb = -ps.s2[1] * idet, qc = ps.s2[0] * idet;
-  // 2D gradients in natural units
-  const float gmu2x = -kLn2 * ga.x, gmu2y = -kLn2 * ga.y;
-  const float gA = -0.5f * ga.z, gB = -ga.w, gC = -0.5f * gb.x;
+  // 2D gradients in natural units: dL/dmu_2D = 2 ln2 (v0, v1) and
+  // dL/dSigma_2D = 2 ln2^2 [[v2, v3], [v3, v4]] (the raster accumulated
+  // z = Sigma^-1 d in units of 1 / (2 ln 2))
+  const float gmu2x = 2.f * kLn2 * ga.x, gmu2y = 2.f * kLn2 * ga.y;
+  const float gs_scale = 2.f * kLn2 * kLn2;
+  const float GS00 = gs_scale * ga.z, GS01 = gs_scale * ga.w, GS11 = gs_scale * gb.x;
   const float grgb[3] = {gb.y, gb.z, gb.w};
   const float gop = gc.x;
   float gmu[3] = {0.f, 0.f, 0.f};
@@ -281,39 +287,21 @@ __device__ __forceinline__ void project_bwd_one(
     }
   }
 
-  // conic -> Sigma_2D: G_S = -Q G_Q Q, G_Q = [[gA, gB/2], [gB/2, gC]]
-  float GS00, GS01, GS11;
-  {
-    const float h = 0.5f * gB;
-    const float t00 = qa * gA + qb * h, t01 = qa * h + qb * gC;
-    const float t10 = qb * gA + qc * h, t11 = qb * h + qc * gC;
-    GS00 = -(t00 * qa + t01 * qb);
-    GS01 = -(t00 * qb + t01 * qc);
-    GS11 = -(t10 * qb + t11 * qc);
-  }
-  // Sigma_2D = Tm S3 Tm^T + 0.3 I:  G_S3 = Tm^T G_S Tm, G_Tm = 2 G_S Tm S3
+  // Sigma_2D = N N^T + 0.3 I:  G_N = 2 G_S N;  N = Tm M:  G_Tm = G_N M^T, G_M = Tm^T G_N
+  const float* N = ps.N;
   const float* T = ps.Tm;
-  float GS3[3][3];
+  float GN[6];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      GS3[i][j] = T[i] * (GS00 * T[j] + GS01 * T[3 + j]) + T[3 + i] * (GS01 * T[j] + GS11 * T[3 + j]);
-  const float S3[3][3] = {{ps.S3[0], ps.S3[1], ps.S3[2]},
-                          {ps.S3[1], ps.S3[3], ps.S3[4]},
-                          {ps.S3[2], ps.S3[4], ps.S3[5]}};
-  float TS[2][3];
+  for (int j = 0; j < 3; ++j) {
+    GN[j] = 2.f * (GS00 * N[j] + GS01 * N[3 + j]);
+    GN[3 + j] = 2.f * (GS01 * N[j] + GS11 * N[3 + j]);
+  }
+  float GT[2][3];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-      TS[i][j] = T[i * 3] * S3[0][j] + T[i * 3 + 1] * S3[1][j] + T[i * 3 + 2] * S3[2][j];
-  float GT[2][3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    GT[0][j] = 2.f * (GS00 * TS[0][j] + GS01 * TS[1][j]);
-    GT[1][j] = 2.f * (GS01 * TS[0][j] + GS11 * TS[1][j]);
-  }
+    for (int k = 0; k < 3; ++k)
+      GT[i][k] = GN[i * 3] * ps.M[k * 3] + GN[i * 3 + 1] * ps.M[k * 3 + 1] + GN[i * 3 + 2] * ps.M[k * 3 + 2];
   // Tm = J W:  G_J = G_Tm W^T (only J00, J02, J11, J12 depend on t)
   const float* W = cam.R;
   const float GJ00 = GT[0][0] * W[0] + GT[0][1] * W[1] + GT[0][2] * W[2];
@@ -330,17 +318,17 @@ __device__ __forceinline__ void project_bwd_one(
 #pragma unroll
   for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt[0] + W[3 + j] * gt[1] + W[6 + j] * gt[2];
 
-  // Sigma_3D = M M^T: G_M = 2 G_S3 M; M_ij = R_ij s_j
+  // M_kj = R_kj s_j:  dL/ds_j = sum_k G_M_kj R_kj,  G_R_kj = G_M_kj s_j
   const float s[3] = {sx, sy, sz};
   float gs[3] = {0.f, 0.f, 0.f};
   float GR[9];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const float gm = 2.f * (GS3[i][0] * ps.M[j] + GS3[i][1] * ps.M[3 + j] + GS3[i][2] * ps.M[6 + j]);
-      gs[j] += ps.R[i * 3 + j] * gm;
-      GR[i * 3 + j] = gm * s[j];
+      const float gm = T[k] * GN[j] + T[3 + k] * GN[3 + j];
+      gs[j] += ps.R[k * 3 + j] * gm;
+      GR[k * 3 + j] = gm * s[j];
     }
   // R(q_hat) -> q_hat -> q
   const float w = ps.qn[0], x = ps.qn[1], y = ps.qn[2], z = ps.qn[3];

@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(kBlockPixels) raster_fwd_kernel(
         if (done) continue;
         const float4 a = s_a[j];
         const float4 b = s_b[j];
-        float dx, dy;
-        const float p2 = frag_power2(px, py, a, b, dx, dy);
-        if (p2 < b.y) continue;            // alpha < 1/255
+        float y1, y2;
+        const float q = frag_q(px, py, a, b, y1, y2);
+        if (q > b.y) continue;             // alpha < 1/255
         const float4 c = s_c[j];
         float G, at;
-        const float alpha = frag_alpha(c.w, p2, G, at);
+        const float alpha = frag_alpha(c.w, q, G, at);
         const float w = __fmul_rn(alpha, T);
         C0 = __fmaf_rn(w, c.x, C0);
         C1 = __fmaf_rn(w, c.y, C1);
@@ -229,13 +229,13 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
           } else {
             const float4 a = s_a[j];
             const float4 b = s_b[j];
-            float dx, dy;
-            const float p2 = frag_power2(px, py, a, b, dx, dy);
-            if (p2 >= b.y) {
+            float y1, y2;
+            const float q = frag_q(px, py, a, b, y1, y2);
+            if (q <= b.y) {
               frag = true;
               const float4 c = s_c[j];
               float G, at;
-              const float alpha = frag_alpha(c.w, p2, G, at);
+              const float alpha = frag_alpha(c.w, q, G, at);
               const float oma = __fsub_rn(1.0f, alpha);
               const float wT = __fmul_rn(alpha, T);
               // Eq. 3
@@ -254,12 +254,16 @@ __global__ void __launch_bounds__(kBlockPixels) raster_bwd_kernel(
               // alpha = min(0.99, o G): no gradient through the clamp
               const float d_at = at < kAlphaMax ? dLda : 0.f;
               v[8] = G * d_at;
+              // z = Sigma^-1 d = L^-T L^-1 d, in units of 1 / (2 ln 2):
+              // dpower/dmu_2D = z and dpower/dSigma_2D = z z^T / 2
               const float w = at * d_at;
-              v[0] = w * (2.f * a.z * dx + a.w * dy);
-              v[1] = w * (a.w * dx + 2.f * b.x * dy);
-              v[2] = w * dx * dx;
-              v[3] = w * dx * dy;
-              v[4] = w * dy * dy;
+              const float z1 = b.x * y2;
+              const float z0 = a.z * y1 - a.w * z1;
+              v[0] = w * z0;
+              v[1] = w * z1;
+              v[2] = w * z0 * z0;
+              v[3] = w * z0 * z1;
+              v[4] = w * z1 * z1;
             }
           }
         }

@@ -47,13 +47,15 @@ def test_projection_records_match_oracle():
     assert np.all(P[vis, 0] == 1.0)
     # float-float screen centre (hi + lo) against the FP64 projection
     np.testing.assert_allclose(rec[vis, 0:2] + rec[vis, 6:8], P[vis, 1:3], rtol=0, atol=2e-6)
-    a = rec[vis, 2] / (-0.5 * LOG2E)
-    b = rec[vis, 3] / (-LOG2E)
-    c = rec[vis, 4] / (-0.5 * LOG2E)
-    np.testing.assert_allclose(np.stack([a, b, c], 1), P[vis, 6:9], rtol=2e-4, atol=1e-6)
+    # inverse Cholesky factor (i11, k, i22), scaled by sqrt(log2(e) / 2) -> conic
+    sc2 = 0.5 * LOG2E
+    i11, k, i22 = rec[vis, 2] ** 2 / sc2, rec[vis, 3], rec[vis, 4] ** 2 / sc2
+    conic = np.stack([i11 + k * k * i22, -k * i22, i22], 1)
+    scale = np.maximum(P[vis, 6], P[vis, 8])[:, None]     # each splat's matrix scale
+    assert np.max(np.abs(conic - P[vis, 6:9]) / scale) < 2e-5
     np.testing.assert_allclose(rec[vis, 8:11], P[vis, 9:12], rtol=0, atol=2e-5)
     o = scene_np.opacities.astype(np.float64)
-    np.testing.assert_allclose(rec[vis, 5], np.log2(1.0 / (255.0 * o[vis])), rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(rec[vis, 5], np.log2(255.0 * o[vis]), rtol=1e-5, atol=1e-5)
     np.testing.assert_array_equal(rec[vis, 11], o[vis].astype(np.float32))
     np.testing.assert_allclose(keys[vis].view(np.float32), P[vis, 12], rtol=1e-6)
     # every splat the GPU culled has no pixel centre inside its alpha >= 1/255 box
