@@ -267,6 +267,27 @@ int gs_sort_pairs(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* val
                   uint32_t* keys_out, uint32_t* vals_out, int32_t n, int32_t key_bits,
                   gs_stream_t stream);
 
+/* Allocation-free pair sort.  The paper has no counterpart: this entry point
+ * exists for callers that cannot provide device memory at the point of the
+ * call, such as a host application or plugin interface that owns every device
+ * allocation and hands the library only its inputs and outputs, or a
+ * long-running service that fixes its HBM budget at start-up and forbids
+ * allocations afterwards.  It performs the same stable LSD radix sort as
+ * gs_sort_pairs (same arguments and results, keys below 2^key_bits rounded up
+ * to whole bytes, outputs must not alias inputs) but keeps its scratch in one
+ * fixed array inside the library: every GPU that loads the library holds
+ * about 4.3 MB for it until the process exits, and n may not exceed
+ * GS_SORT_NOALLOC_MAX_PAIRS (larger n returns GS_ERR_INVALID_ARG with a
+ * message).  It calls no allocator.  The first call on each device looks the
+ * array up and zeroes it on `stream` before sorting, so make that first call
+ * before any stream capture.  All calls on a device share the array, and it
+ * keeps the last call's contents: calls that overlap on the GPU (on different
+ * streams, or from different threads) race and corrupt each other; order them
+ * on one stream or serialise them. */
+#define GS_SORT_NOALLOC_MAX_PAIRS 262144
+int gs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                          uint32_t* vals_out, int32_t n, int32_t key_bits, gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

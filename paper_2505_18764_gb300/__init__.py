@@ -343,6 +343,19 @@ def sort_pairs(ws: Workspace, keys: torch.Tensor, vals: torch.Tensor, key_bits: 
     return ko, vo
 
 
+def sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
+    """Same sort as sort_pairs, for callers that cannot hand the library any
+    scratch memory: the library keeps a fixed array of its own (at most
+    GS_SORT_NOALLOC_MAX_PAIRS pairs; calls overlapping on the GPU race)."""
+    if keys.dtype != torch.int32 or vals.dtype != torch.int32 or keys.numel() != vals.numel():
+        raise ValueError("keys and vals must be int32 tensors of the same size")
+    ko, vo = torch.empty_like(keys), torch.empty_like(vals)
+    check(_lib.load().gs_sort_pairs_noalloc(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo),
+                                            keys.numel(), key_bits, _stream(stream)),
+          "gs_sort_pairs_noalloc")
+    return ko, vo
+
+
 @dataclass
 class Request:
     """One gs_render_batch request (tensors must outlive the call's GPU work)."""
@@ -403,5 +416,5 @@ def render_batch(requests, ws: Workspace, stream=None):
 __all__ = ["RasterOpts", "SceneTensors", "Workspace", "project", "sort", "raster_forward", "bin",
            "blend_forward", "blend_backward", "project_backward",
            "raster_backward", "loss", "render", "render_batch", "Request", "check_status",
-           "read_counters", "copy_array", "sort_pairs", "decode_state", "alloc_state",
+           "read_counters", "copy_array", "sort_pairs", "sort_pairs_noalloc", "decode_state", "alloc_state",
            "camera_to_c", "GsError", "zero_grads", "NONE_RANK"]

@@ -24,6 +24,7 @@ GS_STATE_FP32, GS_STATE_FP16, GS_STATE_UNORM16, GS_STATE_UNORM8 = 0, 1, 2, 3
 GS_REDUCE_BLOCK, GS_REDUCE_WARP, GS_REDUCE_NAIVE = 0, 1, 2
 GS_MODE_FORWARD, GS_MODE_FORWARD_BACKWARD = 0, 1
 GS_LOSS_NONE, GS_LOSS_L1, GS_LOSS_L2 = 0, 1, 2
+GS_SORT_NOALLOC_MAX_PAIRS = 262144
 (GS_ARRAY_SORTED_IDS, GS_ARRAY_DEPTH_KEYS, GS_ARRAY_RECORDS, GS_ARRAY_PAIR_BLOCKS,
  GS_ARRAY_PAIR_RANKS, GS_ARRAY_RANGES, GS_ARRAY_GRAD2D, GS_ARRAY_BOXES) = range(8)
 
@@ -89,6 +90,7 @@ _SIGS = {
     "gs_copy_array": [POINTER(GsWorkspace), c_int32, c_void_p, c_size_t, c_void_p],
     "gs_sort_pairs": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                       c_int32, c_void_p],
+    "gs_sort_pairs_noalloc": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p],
 }
 
 EXPORTED = tuple(_SIGS) + ("gs_last_error",)

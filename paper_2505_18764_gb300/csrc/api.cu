@@ -178,6 +178,9 @@ int pair_passes_for(int blocks) {
 }
 
 }  // namespace
+
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 }  // namespace gsr
 
 using namespace gsr;
