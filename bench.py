@@ -210,9 +210,11 @@ def run_ours(args, rank, world, local_rank):
     n_front = int(((scene.means @ torch.as_tensor(cam.viewmat[2, :3], device=dev)) +
                    float(cam.viewmat[2, 3]) > 0.2).sum().item())
     V, P = cnt["visible"], cnt["pairs"]
+    rg = gs.copy_array(ws, _lib.GS_ARRAY_RANGES, cnt["blocks"], stream).to(torch.int64)
+    P_live = int((rg[:, 1] - rg[:, 0]).sum().item())
     npix = H * W
     passes = ws.c.pair_passes
-    kernels_per_step = 1 + 4 + (2 + passes) + 1 + 1 + 1 + 1
+    kernels_per_step = 1 + 4 + (2 + passes + 2) + 1 + 1 + 1 + 1   # bin: count, emit, passes, ranges, order
     K_sh = 16
 
     # algorithmic bytes (HBM-bound stages) and flops (raster stages) per launch
@@ -261,7 +263,8 @@ def run_ours(args, rank, world, local_rank):
                            state_format="fp32", t_cull=1e-4, reduce="block", loss="l1",
                            views_per_step=world, parallelism=f"replicas x{world}",
                            l2="inputs larger than L2 (scene parameters 708 MB > 129 MB)"),
-               counts=dict(visible=V, pairs=P, fragments=F, in_front=n_front, pixels=npix),
+               counts=dict(visible=V, pairs=P, live_pairs=P_live, fragments=F, in_front=n_front,
+                           pixels=npix),
                splat_frags_per_s=round(F / (ms_per_view * 1e-3), 1),
                stages_ms=per_stage, stage_roofline=stage_roof,
                p50_ms=round(float(np.percentile(step_ms, 50)), 4),

@@ -241,7 +241,8 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
  * r, g, b, o: the screen centre mu + mu_lo as a float-float pair, the inverse
  * Cholesky factor of Sigma_2D scaled so that (i11 dx)^2 + (i22 (dy - k dx))^2 =
  * -log2(e) * power, and tau = log2(255 o)),
- * GS_ARRAY_PAIR_BLOCKS u32 [P], GS_ARRAY_PAIR_RANKS u32 [P] (sorted by block),
+ * GS_ARRAY_PAIR_BLOCKS u32 [P], GS_ARRAY_PAIR_RANKS u32 [P] (sorted by block; a
+ * block id equal to the block count marks a box block the ellipse misses),
  * GS_ARRAY_RANGES u32 [blocks][2], GS_ARRAY_GRAD2D float [V][12] (per depth
  * rank: the backward's unscaled accumulators), GS_ARRAY_BOXES u32 [V][2] (per
  * depth rank: first block x | y << 16, box width | height << 16 in blocks). */

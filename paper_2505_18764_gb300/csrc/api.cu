@@ -26,13 +26,15 @@ cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cu
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
 cudaError_t launch_bin(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*, Header*,
                        unsigned long long*, const uint32_t*, uint32_t*, uint2*, uint32_t*, uint32_t*,
-                       uint32_t*, uint32_t, int, int, int, int, cudaStream_t);
-cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, cudaStream_t);
-cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const SplatRec*, int, int, int, int,
-                              float, int, float*, void*, uint32_t*, uint32_t*, cudaStream_t);
-cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const SplatRec*, int, int, int, int,
-                              float, int, const void*, const uint32_t*, const float*, float*, int,
-                              int, cudaStream_t);
+                       uint32_t*, uint32_t, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, int, cudaStream_t);
+cudaError_t launch_block_order(const uint2*, int, uint32_t*, cudaStream_t);
+cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const uint32_t*, const SplatRec*, int,
+                              int, int, int, float, int, float*, void*, uint32_t*, uint32_t*,
+                              cudaStream_t);
+cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, const SplatRec*, int,
+                              int, int, int, float, int, const void*, const uint32_t*, const float*,
+                              float*, int, int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
                         cudaStream_t);
 size_t sort_tiles(size_t n);
@@ -96,6 +98,7 @@ enum Slot {
   L_CHUNKS,      // [pair_cap / 2048 + 1] first depth rank of each emission chunk
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
+  L_ORDER,       // [blocks_cap] u32 launch order of the blocks (longest list first)
   L_END
 };
 
@@ -132,6 +135,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
+  sz[L_ORDER] = blocks * 4;
   size_t o = 0;
   for (int i = 0; i < L_END; ++i) {
     off[i] = o;
@@ -258,7 +262,7 @@ int gs_project(gs_workspace* ws, const float* means, const float* scales, const 
   ws->sh_degree = opts->sh_degree;
   ws->state_format = opts->state_format;
   ws->clamp01 = opts->state_format == GS_STATE_UNORM16 || opts->state_format == GS_STATE_UNORM8;
-  ws->pair_passes = pair_passes_for(blocks);
+  ws->pair_passes = pair_passes_for(blocks + 1);   // ids 0..blocks (blocks = missed)
   GS_CUDA(cudaMemsetAsync(at<Header>(ws, L_HDR), 0, sizeof(Header), st), "gs_project memset");
   GS_CUDA(launch_project_fwd(means, scales, quats, opacities, sh, n, opts->sh_degree, *cam,
                              ws->clamp01, at<SplatRec>(ws, L_REC), at<uint2>(ws, L_BOXES_ID),
@@ -320,7 +324,7 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
                      at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN), epoch,
                      at<uint32_t>(ws, L_OFFSETS), at<uint2>(ws, L_BOXES), at<uint32_t>(ws, L_CHUNKS),
                      at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PVA), (uint32_t)ws->pair_cap,
-                     gw, ws->pair_passes, ws->n, grid_cap, st),
+                     gw, gh, ws->pair_passes, ws->n, grid_cap, st),
           "bin kernel");
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
   uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};
@@ -333,7 +337,10 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
             "pair sort pass");
   }
   const int fin = ws->pair_passes & 1;
-  GS_CUDA(launch_ranges(pk[fin], hdr, at<uint2>(ws, L_RANGES), num_sms(), st), "ranges kernel");
+  GS_CUDA(launch_ranges(pk[fin], hdr, at<uint2>(ws, L_RANGES), gw * gh, num_sms(), st),
+          "ranges kernel");
+  GS_CUDA(launch_block_order(at<uint2>(ws, L_RANGES), gw * gh, at<uint32_t>(ws, L_ORDER), st),
+          "block order kernel");
   return GS_OK;
 }
 
@@ -347,7 +354,8 @@ int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
-  GS_CUDA(launch_raster_fwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+  GS_CUDA(launch_raster_fwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER),
+                            at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, image, state, last, n_contrib,
                             reinterpret_cast<cudaStream_t>(stream)),
@@ -378,7 +386,8 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
-  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER),
+                            at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, state, last, dL_dimage,
                             at<float>(ws, L_G2D), opts->reduce_mode, opts->reduce_threshold,

@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
 // work is even however the pairs are spread over splats.
 __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
     const uint32_t* __restrict__ offsets, const uint2* __restrict__ boxes,
-    const uint32_t* __restrict__ chunk_rank, Header* __restrict__ hdr,
-    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, int gw, int pair_passes) {
+    const uint32_t* __restrict__ chunk_rank, const SplatRec* __restrict__ rec_sorted,
+    Header* __restrict__ hdr, uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals,
+    int gw, int gh, int pair_passes) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   __shared__ uint2 s_box[kEmitChunk + 1];
   __shared__ uint32_t s_hist[4][256];
@@ -187,7 +188,11 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
       const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
       const uint32_t bx = (box.x & 0xFFFFu) + k % w;
       const uint32_t by = (box.x >> 16) + min(k / w, h - 1);  // stays inside the box
-      const uint32_t key = by * (uint32_t)gw + bx;
+      // blocks of the box that the ellipse misses get the sentinel id gw * gh:
+      // they sort behind every real block and no block's range includes them
+      const SplatRec& R = rec_sorted[r0 + lo];
+      const bool hit = block_may_hit(R.a, R.b, (float)(bx * kBlock) + 0.5f, (float)(by * kBlock) + 0.5f);
+      const uint32_t key = hit ? by * (uint32_t)gw + bx : (uint32_t)(gw * gh);
       pair_keys[p] = key;
       pair_vals[p] = r0 + lo;
       for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
@@ -204,21 +209,68 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
 // zero beforehand (the projection kernel clears them).
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys,
                                                      const Header* __restrict__ hdr,
-                                                     uint2* __restrict__ ranges) {
+                                                     uint2* __restrict__ ranges, uint32_t nblocks) {
   const uint32_t P = hdr->pairs;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
     const uint32_t k = keys[i];
+    if (k >= nblocks) continue;   // pairs whose block the ellipse misses
     if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
     if (i + 1 == P || keys[i + 1] != k) ranges[k].y = i + 1;
   }
+}
+
+// Longest-list-first launch order of the pixel blocks: a counting sort of the
+// blocks by a logarithmic bucket of their list length (descending), in one
+// CTA.  CTAs are dispatched roughly in launch order, so the heaviest blocks
+// start first and the raster's tail shrinks.  The order inside a bucket only
+// affects scheduling, never a result.
+constexpr int kOrderBuckets = 128;
+
+__device__ __forceinline__ int length_bucket(uint32_t len) {
+  if (len == 0) return kOrderBuckets - 1;
+  const int lg = 31 - __clz(len);                       // floor(log2 len), 0..31
+  const int frac = lg >= 2 ? (int)((len >> (lg - 2)) & 3) : 0;  // 4 sub-buckets per octave
+  return kOrderBuckets - 2 - min(lg * 4 + frac, kOrderBuckets - 2);  // long lists first
+}
+
+__global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restrict__ ranges,
+                                                          int nblocks, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  __shared__ uint32_t s_pos[kOrderBuckets];
+  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const uint2 r = ranges[b];
+    atomicAdd(&s_cnt[length_bucket(r.y - r.x)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kOrderBuckets; ++i) {
+      s_pos[i] = run;
+      run += s_cnt[i];
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const uint2 r = ranges[b];
+    const uint32_t pos = atomicAdd(&s_pos[length_bucket(r.y - r.x)], 1u);
+    order[pos] = (uint32_t)b;
+  }
+}
+
+cudaError_t launch_block_order(const uint2* ranges, int nblocks, uint32_t* order, cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  block_order_kernel<<<1, 1024, 0, st>>>(ranges, nblocks, order);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, const uint2* boxes_by_id,
                        SplatRec* rec_sorted, float* g2d, Header* hdr,
                        unsigned long long* scan_status, const uint32_t* epoch, uint32_t* offsets,
                        uint2* boxes, uint32_t* chunk_rank, uint32_t* pair_keys,
-                       uint32_t* pair_vals, uint32_t pair_cap, int gw, int pair_passes, int n_cap,
-                       int grid_cap, cudaStream_t st) {
+                       uint32_t* pair_vals, uint32_t pair_cap, int gw, int gh, int pair_passes,
+                       int n_cap, int grid_cap, cudaStream_t st) {
   int tiles = (n_cap + kBinTile - 1) / kBinTile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > grid_cap) tiles = grid_cap;
@@ -230,14 +282,14 @@ cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, const ui
   int chunks = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
   if (chunks > grid_cap) chunks = grid_cap;
   if (chunks < 1) chunks = 1;
-  bin_emit_kernel<<<chunks, kBinThreads, 0, st>>>(offsets, boxes, chunk_rank, hdr, pair_keys,
-                                                  pair_vals, gw, pair_passes);
+  bin_emit_kernel<<<chunks, kBinThreads, 0, st>>>(offsets, boxes, chunk_rank, rec_sorted, hdr,
+                                                  pair_keys, pair_vals, gw, gh, pair_passes);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges, int num_sms,
-                          cudaStream_t st) {
-  ranges_kernel<<<num_sms * 8, 256, 0, st>>>(keys, hdr, ranges);
+cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges, int nblocks,
+                          int num_sms, cudaStream_t st) {
+  ranges_kernel<<<num_sms * 8, 256, 0, st>>>(keys, hdr, ranges, (uint32_t)nblocks);
   return cudaGetLastError();
 }
 

@@ -86,28 +86,48 @@ __device__ __forceinline__ float next_T(float T, float alpha) {
   return __fmul_rn(T, __fsub_rn(1.0f, alpha));
 }
 
-// Can any pixel centre of a warp's 16x2 strip hold a fragment of this splat?
-// The centres lie on two rows y = ys, ys + 1 and x in [xs, xs + 15]; along a
-// row, q is a convex quadratic in dx whose minimum over the segment is at the
-// clamped vertex.  The margin keeps the test conservative against the
-// rounding of frag_q (it only decides what to skip).
-__device__ __forceinline__ bool strip_may_hit(const float4& a, const float4& b, float xs,
-                                              float ys) {
-  const float X0 = (xs - a.x) - b.z, X1 = X0 + 15.0f;
+// Can any pixel centre of the rectangle [x0, x0 + wx] x [y0, y0 + wy] (pixel
+// centres) hold a fragment of this splat?  q is convex, so its minimum over
+// the rectangle is 0 if the splat's centre lies inside, else on one of the four
+// edges, each a one-dimensional minimum at a clamped vertex.  The margin keeps
+// the test conservative against the rounding of frag_q (it only decides what
+// to skip).
+__device__ __forceinline__ bool rect_may_hit(const float4& a, const float4& b, float x0, float y0,
+                                             float wx, float wy) {
+  const float X0 = (x0 - a.x) - b.z, X1 = X0 + wx;
+  const float Y0 = (y0 - a.y) - b.w, Y1 = Y0 + wy;
+  if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
   const float i11 = a.z, k = a.w, i22 = b.x;
   const float ki = k * i22;
-  const float slope = ki * i22 * __frcp_rn(fmaf(i11, i11, ki * ki));  // vertex dx = slope * dy
+  const float slope = ki * i22 * __frcp_rn(fmaf(i11, i11, ki * ki));  // row vertex dx = slope * dy
   const float lim = b.y + 0.01f + 1e-3f * b.y;
-  bool hit = false;
+  float best = INFINITY;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const float Y = (ys + (float)r - a.y) - b.w;
+  for (int e = 0; e < 2; ++e) {
+    const float Y = e ? Y1 : Y0;                         // horizontal edge
     const float dx = fminf(fmaxf(slope * Y, X0), X1);
     const float y1 = i11 * dx, y2 = i22 * (Y - k * dx);
-    hit |= fmaf(y1, y1, y2 * y2) <= lim;
+    best = fminf(best, fmaf(y1, y1, y2 * y2));
+    const float X = e ? X1 : X0;                         // vertical edge: vertex dy = k dx
+    const float dy = fminf(fmaxf(k * X, Y0), Y1);
+    const float z1 = i11 * X, z2 = i22 * (dy - k * X);
+    best = fminf(best, fmaf(z1, z1, z2 * z2));
   }
-  return hit;
+  return best <= lim;
 }
+
+__device__ __forceinline__ bool block_may_hit(const float4& a, const float4& b, float x0,
+                                              float y0) {
+  return rect_may_hit(a, b, x0, y0, 15.0f, 15.0f);
+}
+
+// Asynchronous 16-byte global -> shared copies (bypassing L1) and their fences.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Float-float ("double-float") arithmetic from error-free transformations

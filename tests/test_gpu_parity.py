@@ -110,10 +110,14 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     ranks = gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_RANKS, P).cpu().numpy().astype(np.int64)
     ranges = gs.copy_array(ws, gs._lib.GS_ARRAY_RANGES, cnt["blocks"]).cpu().numpy().astype(np.int64)
     assert np.all(np.diff(blocks) >= 0)
-    same = np.diff(blocks) == 0
+    nblk = cnt["blocks"]
+    live = blocks < nblk
+    same = (np.diff(blocks) == 0) & live[1:]
     assert np.all(np.diff(ranks)[same] > 0), "depth order lost inside a block"
+    assert np.all(np.diff(ranks)[~live[1:] & ~live[:-1]] >= 0)   # missed blocks keep rank order
+    assert np.all(blocks[~live] == nblk) and live.sum() > 0
     # ranges delimit each block's run
-    for b in np.unique(blocks):
+    for b in np.unique(blocks[live]):
         s, e = ranges[b]
         assert np.all(blocks[s:e] == b) and (s == 0 or blocks[s - 1] != b) and (e == P or blocks[e] != b)
     # each splat's pairs are exactly the blocks of its box, and every box holds
@@ -123,9 +127,9 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     w, h = boxes[:, 1] & 0xFFFF, boxes[:, 1] >> 16
     np.testing.assert_array_equal(np.bincount(ranks, minlength=V), w * h)
     gw = (cam.width + 15) // 16
-    pbx, pby = blocks % gw, blocks // gw
-    assert np.all((pbx >= bx0[ranks]) & (pbx < bx0[ranks] + w[ranks]) &
-                  (pby >= by0[ranks]) & (pby < by0[ranks] + h[ranks]))
+    pbx, pby = blocks[live] % gw, blocks[live] // gw
+    rl = ranks[live]
+    assert np.all((pbx >= bx0[rl]) & (pbx < bx0[rl] + w[rl]) & (pby >= by0[rl]) & (pby < by0[rl] + h[rl]))
     ids = gs.copy_array(ws, gs._lib.GS_ARRAY_SORTED_IDS, V).cpu().numpy()
     Pj = oracle.project(scene_np, cam)[ids]
     o = scene_np.opacities[ids].astype(np.float64)
