@@ -464,3 +464,36 @@ def test_fp16_cprime_emulation_changes_little():
         assert 0 < err < 5e-2
     # colour gradients do not depend on C'
     np.testing.assert_allclose(q["sh"], ex["sh"], rtol=1e-12, atol=1e-12)
+
+
+def test_torch_gradcheck_on_oracle_binding():
+    """torch.autograd.gradcheck (FP64 central differences) on an autograd
+    Function whose forward and backward are the oracle's."""
+    torch = pytest.importorskip("torch")
+
+    bands = dict(band_cut=1e-3, band_clamp=1e-3)
+    seed = 700
+    while True:
+        sc, cam = _fd_scene(seed, n=5, deg=2, size=16)
+        if _clean(sc, cam, oracle.opts_array(t_cull=0.0, **bands)):
+            break
+        seed += 1
+        assert seed < 1000
+    opts = oracle.opts_array(t_cull=0.0)
+
+    class OracleRender(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, m, s, q, o, sh):
+            ctx.save_for_backward(m, s, q, o, sh)
+            scene = syn.Scene(m.numpy(), s.numpy(), q.numpy(), o.numpy(), sh.numpy(), sc.sh_degree)
+            return torch.from_numpy(oracle.render(scene, cam, opts)["color"])
+
+        @staticmethod
+        def backward(ctx, g):
+            m, s, q, o, sh = ctx.saved_tensors
+            scene = syn.Scene(m.numpy(), s.numpy(), q.numpy(), o.numpy(), sh.numpy(), sc.sh_degree)
+            r = oracle.backward(scene, cam, g.numpy(), opts)
+            return tuple(torch.from_numpy(r[k]) for k in ("means", "scales", "quats", "opacities", "sh"))
+
+    inputs = tuple(torch.tensor(a.astype(np.float64), requires_grad=True) for a in sc.arrays())
+    assert torch.autograd.gradcheck(OracleRender.apply, inputs, eps=1e-6, atol=1e-6, rtol=1e-4)
