@@ -141,10 +141,13 @@ typedef struct gs_request {
 int gs_workspace_size(int32_t n_cap, int32_t width_cap, int32_t height_cap,
                       const gs_raster_opts* opts, size_t* bytes);
 
-/* Lays the workspace out in `device_base` (caller-owned, >= bytes).  `ws` is a
- * host struct the caller owns; nothing is allocated. */
+/* Lays the workspace out in `device_base` (caller-owned, >= bytes) and clears
+ * its header and look-back words asynchronously on `stream`; use the workspace
+ * on that stream (or after it).  `ws` is a host struct the caller owns;
+ * nothing is allocated. */
 int gs_workspace_init(gs_workspace* ws, void* device_base, size_t bytes, int32_t n_cap,
-                      int32_t width_cap, int32_t height_cap, const gs_raster_opts* opts);
+                      int32_t width_cap, int32_t height_cap, const gs_raster_opts* opts,
+                      gs_stream_t stream);
 
 /* Per-splat projection (Sec. 2.1.2): t = W mu + w, cull if tz <= znear,
  * Sigma_2D = J W R S S^T R^T W^T J^T + 0.3 I, conic = Sigma_2D^-1,
@@ -232,7 +235,8 @@ const char* gs_last_error(void);
 
 /* Introspection for tests and metrics.  gs_read_counters synchronises `stream`
  * and writes (host) out[0] = visible splats V, out[1] = pairs P, out[2] =
- * device status, out[3] = 16x16 blocks of the bound camera. */
+ * device status, out[3] = 16x16 blocks of the bound camera, out[4] = pairs the
+ * view needs (above out[1] when the pair capacity was exceeded).  out holds 5. */
 int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
 
 /* Copies an internal array of `ws` into caller device memory `dst` (`bytes`):

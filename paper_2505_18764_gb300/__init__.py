@@ -145,27 +145,44 @@ class Workspace:
     """Caller-owned device scratch for one stream (gs_workspace_size / _init)."""
 
     def __init__(self, n_cap: int, width_cap: int, height_cap: int, opts: RasterOpts | None = None,
-                 device=None):
+                 device=None, stream=None, buffer: torch.Tensor | None = None):
+        """`buffer` (uint8 CUDA tensor of at least required_bytes(...) + 256 bytes)
+        lets a caller reuse one allocation for successive workspaces."""
         lib = _lib.load()
         opts = opts or RasterOpts()
         co = opts.to_c()
-        nbytes = ctypes.c_size_t(0)
-        check(lib.gs_workspace_size(n_cap, width_cap, height_cap, ctypes.byref(co),
-                                    ctypes.byref(nbytes)), "gs_workspace_size")
-        self.nbytes = int(nbytes.value)
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.nbytes = Workspace.required_bytes(n_cap, width_cap, height_cap, opts)
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        if buffer is not None:
+            if buffer.numel() < self.nbytes + 256 or buffer.device != self.device:
+                raise ValueError("workspace buffer too small or on another device")
+            self.buf = buffer
+        else:
+            self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
         base = (self.buf.data_ptr() + 255) & ~255
         self.c = _lib.GsWorkspace()
         with torch.cuda.device(self.device):
+            st = stream if stream is not None else torch.cuda.current_stream(self.device)
             check(lib.gs_workspace_init(ctypes.byref(self.c), base, self.nbytes, n_cap, width_cap,
-                                        height_cap, ctypes.byref(co)), "gs_workspace_init")
+                                        height_cap, ctypes.byref(co), _stream(st)),
+                  "gs_workspace_init")
         self.n_cap, self.width_cap, self.height_cap = n_cap, width_cap, height_cap
         self.pair_cap = int(self.c.pair_cap)
 
     @property
     def ref(self):
         return ctypes.byref(self.c)
+
+    @staticmethod
+    def required_bytes(n_cap: int, width_cap: int, height_cap: int, opts: RasterOpts | None = None) -> int:
+        nbytes = ctypes.c_size_t(0)
+        co = (opts or RasterOpts()).to_c()
+        check(_lib.load().gs_workspace_size(n_cap, width_cap, height_cap, ctypes.byref(co),
+                                            ctypes.byref(nbytes)), "gs_workspace_size")
+        return int(nbytes.value)
 
 
 def project(ws: Workspace, scene: SceneTensors, cam, opts: RasterOpts, stream=None):
@@ -311,9 +328,10 @@ def check_status(ws: Workspace, stream=None):
 
 
 def read_counters(ws: Workspace, stream=None) -> dict:
-    out = (ctypes.c_int64 * 4)()
+    out = (ctypes.c_int64 * 5)()
     check(_lib.load().gs_read_counters(ws.ref, out, _stream(stream)), "gs_read_counters")
-    return dict(visible=int(out[0]), pairs=int(out[1]), status=int(out[2]), blocks=int(out[3]))
+    return dict(visible=int(out[0]), pairs=int(out[1]), status=int(out[2]), blocks=int(out[3]),
+                pairs_wanted=int(out[4]))
 
 
 _ARRAY_DTYPES = {

@@ -66,7 +66,7 @@ class GsRequest(Structure):
 _SIGS = {
     "gs_workspace_size": [c_int32, c_int32, c_int32, POINTER(GsRasterOpts), POINTER(c_size_t)],
     "gs_workspace_init": [POINTER(GsWorkspace), c_void_p, c_size_t, c_int32, c_int32, c_int32,
-                          POINTER(GsRasterOpts)],
+                          POINTER(GsRasterOpts), c_void_p],
     "gs_project": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                    c_int32, POINTER(GsCamera), POINTER(GsRasterOpts), c_void_p],
     "gs_sort": [POINTER(GsWorkspace), c_void_p],

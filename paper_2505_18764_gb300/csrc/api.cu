@@ -216,7 +216,8 @@ int gs_workspace_size(int32_t n_cap, int32_t width_cap, int32_t height_cap,
 }
 
 int gs_workspace_init(gs_workspace* ws, void* device_base, size_t bytes, int32_t n_cap,
-                      int32_t width_cap, int32_t height_cap, const gs_raster_opts* opts) {
+                      int32_t width_cap, int32_t height_cap, const gs_raster_opts* opts,
+                      gs_stream_t stream) {
   if (!ws) return fail(GS_ERR_INVALID_ARG, "ws is null");
   size_t need = 0;
   int rc = gs_workspace_size(n_cap, width_cap, height_cap, opts, &need);
@@ -236,9 +237,10 @@ int gs_workspace_init(gs_workspace* ws, void* device_base, size_t bytes, int32_t
   size_t total = 0;
   compute_layout(n_cap, width_cap, height_cap, ws->pair_cap, ws->layout, &total);
   // Header, epoch and all look-back words start at zero (a zero word never
-  // carries a valid tag's flag).  Synchronous: runs once per workspace.
-  GS_CUDA(cudaMemset(device_base, 0, ws->layout[L_SCAN + 1]), "workspace init memset");
-  GS_CUDA(cudaDeviceSynchronize(), "workspace init sync");
+  // carries a valid tag's flag); ordered before later work on `stream`.
+  GS_CUDA(cudaMemsetAsync(device_base, 0, ws->layout[L_SCAN + 1],
+                          reinterpret_cast<cudaStream_t>(stream)),
+          "workspace init memset");
   return GS_OK;
 }
 
@@ -497,7 +499,7 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream) {
   if (rc) return rc;
   if (!out) return fail(GS_ERR_INVALID_ARG, "out is null");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  uint32_t h[4] = {0, 0, 0, 0};
+  uint32_t h[4] = {0, 0, 0, 0};   // status, visible, pairs, pairs_wanted
   GS_CUDA(cudaMemcpyAsync(h, at<Header>(ws, L_HDR), 16, cudaMemcpyDeviceToHost, st), "counter copy");
   GS_CUDA(cudaStreamSynchronize(st), "counter sync");
   int gw, gh;
@@ -505,6 +507,7 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream) {
   out[1] = h[2];
   out[2] = h[0];
   out[3] = blocks_of(ws->width, ws->height, gw, gh);
+  out[4] = h[3];
   return GS_OK;
 }
 

@@ -80,7 +80,7 @@ def test_workspace_size_and_argument_errors(lib):
     assert lib.gs_workspace_size(-1, 128, 128, ctypes.byref(o), ctypes.byref(n)) == _lib.GS_ERR_INVALID_ARG
     ws = _lib.GsWorkspace()
     # a null device pointer is refused before any CUDA call
-    assert lib.gs_workspace_init(ctypes.byref(ws), None, 1 << 20, 10, 16, 16, ctypes.byref(o)) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_workspace_init(ctypes.byref(ws), None, 1 << 20, 10, 16, 16, ctypes.byref(o), None) == _lib.GS_ERR_INVALID_ARG
     # calls on an uninitialised workspace are refused before any CUDA call
     assert lib.gs_sort(ctypes.byref(_lib.GsWorkspace()), None) == _lib.GS_ERR_INVALID_ARG
     assert lib.gs_loss(None, None, 10, 7, None, None, None) == _lib.GS_ERR_INVALID_ARG
