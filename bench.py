@@ -121,6 +121,20 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
+def replica_orbit_angle(rank: int, world: int) -> float:
+    """Each rank renders its own view: orbit angle 2 pi rank / world."""
+    return 2.0 * math.pi * rank / world
+
+
+def max_over_ranks_ms(total_ms: float, device, world: int) -> float:
+    """Elapsed time of the job: the slowest rank's (MAX all-reduce; a no-op at N = 1)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2505_18764_gb300 as gs
@@ -131,7 +145,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     t0 = time.time()
     scene_np, cam0, target_np = syn.mipnerf_scene_3m(args.n)
-    cam = syn.orbit_camera(2.0 * math.pi * rank / world, 4.0, 50.0, cam0.width, cam0.height)
+    cam = syn.orbit_camera(replica_orbit_angle(rank, world), 4.0, 50.0, cam0.width, cam0.height)
     log(f"[rank {rank}] scene generated in {time.time() - t0:.1f}s")
     scene = gs.SceneTensors.from_numpy(scene_np, dev)
     target = torch.from_numpy(target_np).to(dev)
@@ -199,10 +213,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms, per_stage, step_ms, t_wall = timed(step32, args.steps, 0)
     clk = clocks.stop() if not args.no_extras else None
     gs.check_status(ws, stream)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms_max = float(t.item())
+    total_ms_max = max_over_ranks_ms(total_ms, dev, world)
     ms_per_view = total_ms_max / (args.steps * world)
 
     # counters of this view (untimed): visible splats, pairs, fragments
@@ -249,7 +260,8 @@ def run_ours(args, rank, world, local_rank):
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         tj = json.load(open(tfile))
-        if tj.get("kernel_stage") == dom and tj.get("source_hash") == _source_hash():
+        if tj.get("kernel_stage") == dom and \
+                tj.get("source_hash") == _source_hash(tj.get("source_files", [])):
             traffic = tj.get("bytes_per_launch")
     roofline = dict(kernel=dom, bound=dr["bound"], achieved=dr["achieved"],
                     peak=round(hbm_peak, 1) if dr["bound"] == "hbm" else round(FP32_PEAK_TFLOPS, 2),
@@ -372,13 +384,18 @@ def run_serving(args, dev):
     return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in stats.items()}
 
 
-def _source_hash():
+def _source_hash(files):
+    """Hash of the kernel sources the stored DRAM counters were taken from:
+    the counters stand only while those files are unchanged."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2505_18764_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
-    return h.hexdigest()[:16]
+    for f in sorted(files):
+        p = os.path.join(d, f)
+        if not os.path.exists(p):
+            return None
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16] if files else None
 
 
 # ---------------------------------------------------------------------------

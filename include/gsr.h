@@ -84,7 +84,7 @@ typedef struct gs_camera {
 typedef struct gs_raster_opts {
   int32_t state_format;     /* GS_STATE_* */
   int32_t reduce_mode;      /* GS_REDUCE_* */
-  int32_t reduce_threshold; /* X of Sec. 3.2.3: warps with fewer active lanes add directly */
+  int32_t reduce_threshold; /* X of Sec. 3.2.4: warps with fewer active lanes add directly */
   int32_t sh_degree;        /* 0..3 */
   float t_cull;             /* skip fragment i iff T_i < t_cull (Procedure 1); 0 disables */
   int32_t reserved;

@@ -10,7 +10,7 @@
 // fragment processing: a pixel belongs to one thread, so no interlock is
 // needed (the race programmable blending guards against cannot occur), and a
 // splat's fragments are always together in a warp and a CTA (the "cohesion"
-// of Sec. 3.2.2 holds by construction).  Each warp first tests the staged
+// of Sec. 3.2.3 holds by construction).  Each warp first tests the staged
 // splats against its footprint (rect_may_hit) and then walks only those that
 // can touch it.
 //
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
           const uint32_t active = __ballot_sync(0xffffffffu, frag);
           const bool reduce = active != 0u && __popc(active) >= threshold;
           float tot = 0.f;
-          if (active != 0u && !reduce) {    // few lanes: add directly (Sec. 3.2.3)
+          if (active != 0u && !reduce) {    // few lanes: add directly (Sec. 3.2.4)
             if (frag) {
               red_add_v4(gdst, v[0], v[1], v[2], v[3]);
               red_add_v4(gdst + 4, v[4], v[5], v[6], v[7]);
