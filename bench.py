@@ -274,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32",
                data="synthetic",
                config=dict(workload=WORKLOAD, splats=scene.n, width=W, height=H, sh_degree=3,
-                           state_format="fp32", t_cull=1e-4, reduce="block", loss="l1",
+                           state_format="fp32", t_cull=1e-4, reduce="warp", loss="l1",
                            views_per_step=world, parallelism=f"replicas x{world}",
                            l2="inputs larger than L2 (scene parameters 708 MB > 129 MB)"),
                counts=dict(visible=V, pairs=P, live_pairs=P_live, fragments=F, in_front=n_front,

@@ -60,11 +60,12 @@ enum {
   GS_STATE_UNORM8 = 3   /* uchar4  (r, g, b, T),  4 B / pixel, colours saturated to [0, 1] */
 };
 
-/* Per-splat gradient reduction in the backward raster (Sec. 3.2). */
+/* Per-splat gradient reduction in the backward raster (Sec. 3.2).  The raster
+ * kernels give each warp a footprint of 64 pixels (16x4) or, in blocks with
+ * long splat lists, 32 pixels (8x4). */
 enum {
-  GS_REDUCE_BLOCK = 0, /* warp transpose-reduce + cross-warp sum: one atomic per (splat, 16x16 block) */
-  GS_REDUCE_WARP = 1,  /* warp reduce: one atomic per (splat, warp) */
-  GS_REDUCE_NAIVE = 2  /* one atomic per fragment (the paper's 1x baseline) */
+  GS_REDUCE_WARP = 0, /* transpose-reduce over the warp: one vector-atomic triple per (splat, footprint) */
+  GS_REDUCE_NAIVE = 1 /* one vector-atomic triple per fragment (the paper's 1x baseline) */
 };
 
 enum { GS_MODE_FORWARD = 0, GS_MODE_FORWARD_BACKWARD = 1 };
@@ -81,13 +82,18 @@ typedef struct gs_camera {
   float znear;
 } gs_camera;
 
+#define GS_SPLIT_THRESHOLD_DEFAULT 2048
+
 typedef struct gs_raster_opts {
   int32_t state_format;     /* GS_STATE_* */
   int32_t reduce_mode;      /* GS_REDUCE_* */
   int32_t reduce_threshold; /* X of Sec. 3.2.4: warps with fewer active lanes add directly */
   int32_t sh_degree;        /* 0..3 */
   float t_cull;             /* skip fragment i iff T_i < t_cull (Procedure 1); 0 disables */
-  int32_t reserved;
+  int32_t split_threshold;  /* blocks whose splat list has at least this many entries are
+                               walked by eight warps (8x4 pixels, one per lane) instead of four
+                               (16x4, two per lane); 0 = default (GS_SPLIT_THRESHOLD_DEFAULT),
+                               1 = every block.  Results do not depend on it. */
   int64_t pair_capacity;    /* (splat, 16x16 block) pairs the workspace holds; 0 = 16 per splat */
 } gs_raster_opts;
 

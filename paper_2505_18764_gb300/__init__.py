@@ -17,7 +17,7 @@ from ._lib import (GS_LOSS_L1, GS_LOSS_L2, GS_LOSS_NONE, GS_MODE_FORWARD, GS_MOD
 
 STATE_FORMATS = {"fp32": 0, "fp16": 1, "unorm16": 2, "unorm8": 3}
 STATE_BYTES = {"fp32": 16, "fp16": 8, "unorm16": 8, "unorm8": 4}
-REDUCE_MODES = {"block": 0, "warp": 1, "naive": 2}
+REDUCE_MODES = {"warp": 0, "naive": 1}
 NONE_RANK = 0xFFFFFFFF
 
 
@@ -25,11 +25,12 @@ NONE_RANK = 0xFFFFFFFF
 class RasterOpts:
     """Mirror of gs_raster_opts."""
     state_format: str = "fp32"
-    reduce_mode: str = "block"
+    reduce_mode: str = "warp"
     reduce_threshold: int = 0
     sh_degree: int = 0
     t_cull: float = 1e-4
     pair_capacity: int = 0
+    split_threshold: int = 0
 
     def to_c(self) -> _lib.GsRasterOpts:
         o = _lib.GsRasterOpts()
@@ -39,6 +40,7 @@ class RasterOpts:
         o.sh_degree = int(self.sh_degree)
         o.t_cull = float(self.t_cull)
         o.pair_capacity = int(self.pair_capacity)
+        o.split_threshold = int(self.split_threshold)
         return o
 
 

@@ -28,13 +28,14 @@ cudaError_t launch_bin(const uint32_t*, const SplatRec*, const uint2*, SplatRec*
                        unsigned long long*, const uint32_t*, uint32_t*, uint2*, uint32_t*, uint32_t*,
                        uint32_t*, uint32_t, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, int, cudaStream_t);
-cudaError_t launch_block_order(const uint2*, int, uint32_t*, cudaStream_t);
-cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const uint32_t*, const SplatRec*, int,
-                              int, int, int, float, int, float*, void*, uint32_t*, uint32_t*,
+cudaError_t launch_block_order(const uint2*, int, uint32_t, uint32_t*, Header*, cudaStream_t);
+cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint32_t*,
+                              const uint32_t*, const SplatRec*, int, int, int, int, float, int,
+                              float*, void*, uint32_t*, uint32_t*, int, cudaStream_t);
+cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const Header*, uint32_t*,
+                              const uint32_t*, const SplatRec*, int, int, int, int, float, int,
+                              const void*, const uint32_t*, const float*, float*, int, int, int,
                               cudaStream_t);
-cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, const SplatRec*, int,
-                              int, int, int, float, int, const void*, const uint32_t*, const float*,
-                              float*, int, int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
                         cudaStream_t);
 size_t sort_tiles(size_t n);
@@ -98,7 +99,7 @@ enum Slot {
   L_CHUNKS,      // [pair_cap / 2048 + 1] first depth rank of each emission chunk
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
-  L_ORDER,       // [blocks_cap] u32 launch order of the blocks (longest list first)
+  L_ORDER,       // [8 blocks_cap] u32 raster work items (warp footprints), longest lists first
   L_END
 };
 
@@ -135,7 +136,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
-  sz[L_ORDER] = blocks * 4;
+  sz[L_ORDER] = blocks * 8 * 4;
   size_t o = 0;
   for (int i = 0; i < L_END; ++i) {
     off[i] = o;
@@ -153,7 +154,8 @@ T* at(const gs_workspace* ws, int slot) {
 int check_opts(const gs_raster_opts* o) {
   if (!o) return fail(GS_ERR_INVALID_ARG, "opts is null");
   if (o->state_format < 0 || o->state_format > 3) return fail(GS_ERR_INVALID_ARG, "bad state_format %d", o->state_format);
-  if (o->reduce_mode < 0 || o->reduce_mode > 2) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
+  if (o->reduce_mode < 0 || o->reduce_mode > 1) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
+  if (o->split_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad split_threshold %d", o->split_threshold);
   if (o->sh_degree < 0 || o->sh_degree > kMaxShDegree) return fail(GS_ERR_INVALID_ARG, "bad sh_degree %d", o->sh_degree);
   if (!(o->t_cull >= 0.f && o->t_cull <= 1.f)) return fail(GS_ERR_INVALID_ARG, "t_cull must be in [0, 1]");
   if (o->pair_capacity < 0 || o->pair_capacity >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [0, 2^30)");
@@ -341,7 +343,10 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
   const int fin = ws->pair_passes & 1;
   GS_CUDA(launch_ranges(pk[fin], hdr, at<uint2>(ws, L_RANGES), gw * gh, num_sms(), st),
           "ranges kernel");
-  GS_CUDA(launch_block_order(at<uint2>(ws, L_RANGES), gw * gh, at<uint32_t>(ws, L_ORDER), st),
+  const uint32_t split = opts->split_threshold > 0 ? (uint32_t)opts->split_threshold
+                                                    : (uint32_t)GS_SPLIT_THRESHOLD_DEFAULT;
+  GS_CUDA(launch_block_order(at<uint2>(ws, L_RANGES), gw * gh, split, at<uint32_t>(ws, L_ORDER),
+                             hdr, st),
           "block order kernel");
   return GS_OK;
 }
@@ -356,11 +361,12 @@ int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
-  GS_CUDA(launch_raster_fwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER),
-                            at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+  Header* hdr = at<Header>(ws, L_HDR);
+  GS_CUDA(launch_raster_fwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER), hdr,
+                            &hdr->raster_next[0], at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, image, state, last, n_contrib,
-                            reinterpret_cast<cudaStream_t>(stream)),
+                            num_sms(), reinterpret_cast<cudaStream_t>(stream)),
           "raster forward kernel");
   return GS_OK;
 }
@@ -388,12 +394,13 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
-  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER),
-                            at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+  Header* hdr = at<Header>(ws, L_HDR);
+  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER), hdr,
+                            &hdr->raster_next[1], at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, state, last, dL_dimage,
                             at<float>(ws, L_G2D), opts->reduce_mode, opts->reduce_threshold,
-                            reinterpret_cast<cudaStream_t>(stream)),
+                            num_sms(), reinterpret_cast<cudaStream_t>(stream)),
           "raster backward kernel");
   return GS_OK;
 }

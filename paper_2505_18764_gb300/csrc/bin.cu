@@ -233,15 +233,21 @@ __device__ __forceinline__ int length_bucket(uint32_t len) {
   return kOrderBuckets - 2 - min(lg * 4 + frac, kOrderBuckets - 2);  // long lists first
 }
 
+// Raster work items, longest lists first: a counting sort of the blocks by
+// length bucket, each block writing its items contiguously (four 16x4 bands,
+// or eight 8x4 cells when its list has at least `split` entries; see
+// raster.cu for the encoding).  The item count goes to the header.
 __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restrict__ ranges,
-                                                          int nblocks, uint32_t* __restrict__ order) {
+                                                          int nblocks, uint32_t split,
+                                                          uint32_t* __restrict__ items,
+                                                          Header* __restrict__ hdr) {
   __shared__ uint32_t s_cnt[kOrderBuckets];
   __shared__ uint32_t s_pos[kOrderBuckets];
   for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const uint2 r = ranges[b];
-    atomicAdd(&s_cnt[length_bucket(r.y - r.x)], 1u);
+    const uint32_t len = ranges[b].y - ranges[b].x;
+    atomicAdd(&s_cnt[length_bucket(len)], len >= split ? 8u : 4u);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -250,18 +256,22 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restri
       s_pos[i] = run;
       run += s_cnt[i];
     }
+    hdr->n_items = run;
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const uint2 r = ranges[b];
-    const uint32_t pos = atomicAdd(&s_pos[length_bucket(r.y - r.x)], 1u);
-    order[pos] = (uint32_t)b;
+    const uint32_t len = ranges[b].y - ranges[b].x;
+    const bool fine = len >= split;
+    const uint32_t n = fine ? 8u : 4u;
+    const uint32_t pos = atomicAdd(&s_pos[length_bucket(len)], n);
+    for (uint32_t k = 0; k < n; ++k) items[pos + k] = ((uint32_t)b << 4) | (fine ? 8u + k : k);
   }
 }
 
-cudaError_t launch_block_order(const uint2* ranges, int nblocks, uint32_t* order, cudaStream_t st) {
+cudaError_t launch_block_order(const uint2* ranges, int nblocks, uint32_t split, uint32_t* items,
+                               Header* hdr, cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
-  block_order_kernel<<<1, 1024, 0, st>>>(ranges, nblocks, order);
+  block_order_kernel<<<1, 1024, 0, st>>>(ranges, nblocks, split, items, hdr);
   return cudaGetLastError();
 }
 

@@ -36,7 +36,9 @@ struct Header {
                               // [8] bin scan, [9..] standalone sort
   uint32_t depth_hist[4][256];
   uint32_t pair_hist[4][256];
-  uint32_t spare[64];
+  uint32_t n_items;            // raster work items (warp footprints) of the last binning
+  uint32_t raster_next[2];     // next item to take: [0] forward, [1] backward
+  uint32_t spare[61];
 };
 
 // Projected splat record, 48 B (three float4):
@@ -128,6 +130,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Float-float ("double-float") arithmetic from error-free transformations

@@ -1,18 +1,24 @@
-// Forward and backward rasterization over 16x16 pixel blocks.
+// Forward and backward rasterization.
 //
-// One CTA of 128 threads per block; each thread owns two pixels of one column
-// (rows r and r + 2 of its warp's 16x4 band), so every warp covers a compact
-// 16x4 footprint with two independent per-pixel dependency chains per lane.
-// The block's depth-ordered splat list is staged into shared memory 256
-// records at a time (asynchronous copies, double-buffered); every thread walks
-// the same splat sequence, so all fragments a block produces for one splat
-// are evaluated together.  That is the CUDA counterpart of the paper's ordered
-// fragment processing: a pixel belongs to one thread, so no interlock is
-// needed (the race programmable blending guards against cannot occur), and a
-// splat's fragments are always together in a warp and a CTA (the "cohesion"
-// of Sec. 3.2.3 holds by construction).  Each warp first tests the staged
-// splats against its footprint (rect_may_hit) and then walks only those that
-// can touch it.
+// Work is cut into warp-sized items.  An item is a rectangle of pixels (the
+// warp's footprint) inside one 16x16 block; the warp walks that block's
+// depth-ordered splat list on its own, staging 32 records at a time into a
+// private ring in shared memory (asynchronous copies, kStages groups in
+// flight), so warps never wait for one another.  A block is cut into four
+// 16x4 footprints with two pixels per lane (rows r and r + 2), or, when its
+// list is long, into eight 8x4 footprints with one pixel per lane: a block
+// under a pile of small splats is then walked by twice as many warps, each
+// meeting fewer candidates, instead of setting the launch time on its own.
+// Persistent CTAs take items from a counter in the order the binning wrote
+// them (longest lists first).
+//
+// That is the CUDA counterpart of the paper's ordered fragment processing: a
+// pixel belongs to one lane, which meets the block's splats in depth order, so
+// no interlock is needed (the race programmable blending guards against cannot
+// occur), and a splat's fragments in a footprint are evaluated together by one
+// warp (the "cohesion" of Sec. 3.2.3 holds by construction).  Each warp first
+// tests the staged splats against its footprint (rect_may_hit) and then walks
+// only those that can touch it.
 //
 // Forward (Eq. 2, Sec. 2.1.2): alpha = min(0.99, o exp(power)), fragments with
 // alpha < 1/255 skipped, T-culling skips fragment i iff T_i < t_cull
@@ -22,51 +28,79 @@
 // Backward (Procedure 1): (C', T) start at (stored C, 1); per fragment
 // dL/dc = g alpha T (Eq. 3), dL/dalpha = g . (c T - C') / (1 - alpha) (Eq. 7),
 // then C' -= T alpha c (Eq. 6) and T *= 1 - alpha (Eq. 5).  The chain rule to
-// the 2D splat parameters follows; the nine per-fragment values of a thread's
-// two pixels are added, reduced over the warp by a transpose-reduce and over
-// the CTA's warps in shared memory, so one vector-atomic triple per
-// (splat, block) reaches global memory (Procedure 2's role).
+// the 2D splat parameters follows; the nine per-fragment values of a lane's
+// pixels are added, reduced over the warp by a transpose-reduce, and one
+// vector-atomic triple per (splat, footprint) reaches global memory
+// (Procedure 2's role).
 #include "common.cuh"
 
 namespace gsr {
 
-constexpr int kThreads = 128;                 // 4 warps, two pixels each per lane
+constexpr int kThreads = 128;                 // 4 independent warps per CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kBatch = 256;                   // records staged per round
-constexpr int kRecPerThread = kBatch / kThreads;
+constexpr int kStages = 4;                    // groups of 32 records in flight per warp
+constexpr unsigned kFull = 0xffffffffu;
 
-struct Stage {
-  float4 a[kBatch];
-  float4 b[kBatch];
-  float4 c[kBatch];
-  uint32_t rank[kBatch];
+// Item encoding: block << 4 | code; code 0..3 = 16x4 band (two pixels per
+// lane), code 8..15 = 8x4 cell (one pixel per lane).
+constexpr uint32_t kFineCode = 8u;
+
+struct WarpRing {
+  float4 a[kStages][32];
+  float4 b[kStages][32];
+  float4 c[kStages][32];
+  uint32_t rank[kStages][32];
 };
 
-// Issue the copies of batch [s, min(s + kBatch, end)) into `st`; `rk` holds the
-// depth ranks of this thread's records (loaded one batch earlier).
-__device__ __forceinline__ void stage_issue(Stage& st, const SplatRec* __restrict__ rec,
-                                            uint32_t s, uint32_t end,
-                                            const uint32_t (&rk)[kRecPerThread]) {
-#pragma unroll
-  for (int u = 0; u < kRecPerThread; ++u) {
-    const int t = threadIdx.x + u * kThreads;
-    if (s + t < end) {
-      const SplatRec* g = rec + rk[u];
-      cp_async16(&st.a[t], &g->a);
-      cp_async16(&st.b[t], &g->b);
-      cp_async16(&st.c[t], &g->c);
-      st.rank[t] = rk[u];
-    }
+// Copy the records of list entries [i - lane, i - lane + 32) (this lane's is i)
+// into ring slot `slot`; `rk` is this lane's depth rank, loaded beforehand.
+// Every call commits one copy group, empty or not, so wait_group counts slots.
+__device__ __forceinline__ void ring_issue(WarpRing& R, int slot, const SplatRec* __restrict__ rec,
+                                           uint32_t i, uint32_t end, uint32_t rk, int lane) {
+  if (i < end) {
+    const SplatRec* g = rec + rk;
+    cp_async16(&R.a[slot][lane], &g->a);
+    cp_async16(&R.b[slot][lane], &g->b);
+    cp_async16(&R.c[slot][lane], &g->c);
+    R.rank[slot][lane] = rk;
   }
   cp_async_commit();
 }
 
-__device__ __forceinline__ void load_ranks(const uint32_t* __restrict__ pair_ranks, uint32_t s,
-                                           uint32_t end, uint32_t (&rk)[kRecPerThread]) {
+// Fill all slots with the first kStages groups of [beg, end).
+__device__ __forceinline__ void ring_start(WarpRing& R, const SplatRec* __restrict__ rec,
+                                           const uint32_t* __restrict__ pair_ranks, uint32_t beg,
+                                           uint32_t end, int lane) {
+  uint32_t rk[kStages];
 #pragma unroll
-  for (int u = 0; u < kRecPerThread; ++u) {
-    const uint32_t i = s + threadIdx.x + u * kThreads;
-    rk[u] = i < end ? pair_ranks[i] : 0u;
+  for (int s = 0; s < kStages; ++s) {
+    const uint32_t i = beg + 32u * s + lane;
+    rk[s] = i < end ? __ldg(pair_ranks + i) : 0u;
+  }
+#pragma unroll
+  for (int s = 0; s < kStages; ++s) ring_issue(R, s, rec, beg + 32u * s + lane, end, rk[s], lane);
+}
+
+// Next item index for this warp (one atomic per warp), or >= n_items when none are left.
+__device__ __forceinline__ uint32_t next_item(uint32_t* counter, int lane) {
+  uint32_t idx = 0;
+  if (lane == 0) idx = atomicAdd(counter, 1u);
+  return __shfl_sync(kFull, idx, 0);
+}
+
+__device__ __forceinline__ void item_origin(uint32_t it, int gw, int& block, int& x0, int& y0,
+                                            bool& fine) {
+  block = (int)(it >> 4);
+  const int code = (int)(it & 15u);
+  const int bx = block % gw, by = block / gw;
+  fine = code >= (int)kFineCode;
+  if (!fine) {
+    x0 = bx * kBlock;
+    y0 = by * kBlock + 4 * code;
+  } else {
+    const int c = code - (int)kFineCode;
+    x0 = bx * kBlock + 8 * (c & 1);
+    y0 = by * kBlock + 4 * (c >> 1);
   }
 }
 
@@ -106,64 +140,87 @@ __device__ __forceinline__ void write_fwd(const PixelFwd& p, int x, int y, int W
   if (ncontrib) ncontrib[pix] = p.n;
 }
 
+// One warp, one footprint: NPX = 2 for a 16x4 band (rows r, r + 2 per lane),
+// NPX = 1 for an 8x4 cell.
+template <int NPX>
+__device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict__ rec,
+                                         const uint32_t* __restrict__ pair_ranks, uint2 range,
+                                         int x0, int y0, int lane, int W, int H, float t_cull,
+                                         int fmt, float* image, void* state, uint32_t* last_out,
+                                         uint32_t* ncontrib) {
+  constexpr int kCols = NPX == 2 ? 16 : 8;
+  const int x = x0 + lane % kCols;
+  const int ya = y0 + lane / kCols, yb = ya + 2;
+  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
+  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
+  PixelFwd pa{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(x < W && ya < H)};
+  PixelFwd pb{1.f, 0.f, 0.f, 0.f, kNone, 0u, NPX == 1 || !(x < W && yb < H)};
+
+  const uint32_t beg = range.x, end = range.y;
+  if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
+  int slot = 0;
+  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kStages - 1)) {
+    const uint32_t ip = gs + 32u * kStages + lane;      // this lane's entry of the refill
+    const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
+    cp_async_wait_group<kStages - 1>();
+    __syncwarp();
+    if (__all_sync(kFull, pa.done && pb.done)) break;
+    const uint32_t cnt = min(32u, end - gs);
+    uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
+                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
+                                                       (float)(kCols - 1), 3.f));
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const float4 a = R.a[slot][j];
+      const float4 b = R.b[slot][j];
+      float y1, y2;
+      const float qa = frag_q(px, pya, a, b, y1, y2);
+      const bool ha = !pa.done && qa <= b.y;   // alpha >= 1/255
+      float qb = 0.f;
+      bool hb = false;
+      if (NPX == 2) {
+        qb = frag_q(px, pyb, a, b, y1, y2);
+        hb = !pb.done && qb <= b.y;
+      }
+      if (!(ha || hb)) continue;
+      const float4 c = R.c[slot][j];
+      const uint32_t rank = R.rank[slot][j];
+      float G, at;
+      if (ha) blend(pa, frag_alpha(c.w, qa, G, at), c, rank, t_cull);
+      if (NPX == 2 && hb) blend(pb, frag_alpha(c.w, qb, G, at), c, rank, t_cull);
+    }
+    __syncwarp();   // every lane is done with the slot before it is refilled
+    ring_issue(R, slot, rec, ip, end, rk_next, lane);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
+  if (NPX == 2) write_fwd(pb, x, yb, W, H, fmt, image, state, last_out, ncontrib);
+}
+
 __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ items,
+    const Header* __restrict__ hdr, uint32_t* __restrict__ next,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, float* __restrict__ image, void* __restrict__ state,
     uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib) {
-  __shared__ Stage stg[2];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t tile = order[blockIdx.x];   // longest lists first
-  const int bx = tile % gw, by = tile / gw;
-  const int x = bx * kBlock + (lane & 15);
-  const int ya = by * kBlock + 4 * warp + (lane >> 4), yb = ya + 2;
-  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
-  const float xs = (float)(bx * kBlock) + 0.5f, ys = (float)(by * kBlock + 4 * warp) + 0.5f;
-  const uint2 range = ranges[tile];
-  PixelFwd pa{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(x < W && ya < H)};
-  PixelFwd pb{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(x < W && yb < H)};
-
-  uint32_t rk[kRecPerThread];
-  load_ranks(pair_ranks, range.x, range.y, rk);
-  if (range.x < range.y) stage_issue(stg[0], rec, range.x, range.y, rk);
-  load_ranks(pair_ranks, range.x + kBatch, range.y, rk);
-  int cur = 0;
-  for (uint32_t s = range.x; s < range.y; s += kBatch, cur ^= 1) {
-    cp_async_wait_all();
-    if (__syncthreads_and(pa.done && pb.done)) break;
-    if (s + kBatch < range.y) {     // next batch in flight while this one is blended
-      stage_issue(stg[cur ^ 1], rec, s + kBatch, range.y, rk);
-      load_ranks(pair_ranks, s + 2 * kBatch, range.y, rk);
-    }
-    const Stage& S = stg[cur];
-    const int cnt = min((uint32_t)kBatch, range.y - s);
-    for (int k = 0; k * 32 < cnt; ++k) {
-      if (__all_sync(0xffffffffu, pa.done && pb.done)) break;
-      const int jt = k * 32 + lane;
-      uint32_t m = __ballot_sync(0xffffffffu,
-                                 jt < cnt && rect_may_hit(S.a[jt], S.b[jt], xs, ys, 15.f, 3.f));
-      while (m) {
-        const int j = k * 32 + __ffs(m) - 1;
-        m &= m - 1u;
-        const float4 a = S.a[j];
-        const float4 b = S.b[j];
-        float y1, y2;
-        const float qa = frag_q(px, pya, a, b, y1, y2);
-        const float qb = frag_q(px, pyb, a, b, y1, y2);
-        const bool ha = !pa.done && qa <= b.y;   // alpha >= 1/255
-        const bool hb = !pb.done && qb <= b.y;
-        if (!(ha || hb)) continue;
-        const float4 c = S.c[j];
-        const uint32_t rank = S.rank[j];
-        float G, at;
-        if (ha) blend(pa, frag_alpha(c.w, qa, G, at), c, rank, t_cull);
-        if (hb) blend(pb, frag_alpha(c.w, qb, G, at), c, rank, t_cull);
-      }
-    }
+  __shared__ WarpRing rings[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpRing& R = rings[warp];
+  const uint32_t n_items = hdr->n_items;
+  for (uint32_t idx = next_item(next, lane); idx < n_items; idx = next_item(next, lane)) {
+    int block, x0, y0;
+    bool fine;
+    item_origin(items[idx], gw, block, x0, y0, fine);
+    const uint2 range = ranges[block];
+    if (fine)
+      fwd_item<1>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
+                  last_out, ncontrib);
+    else
+      fwd_item<2>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
+                  last_out, ncontrib);
   }
-  cp_async_wait_all();
-  write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
-  write_fwd(pb, x, yb, W, H, fmt, image, state, last_out, ncontrib);
 }
 
 // ---------------------------------------------------------------------------
@@ -181,24 +238,24 @@ __device__ __forceinline__ float warp_transpose_reduce9(const float v[9], int la
   for (int i = 0; i < 5; ++i) {
     const float lo = v[i];
     const float hi = (i + 5 < 9) ? v[i + 5] : 0.f;
-    k1[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+    k1[i] = (b4 ? hi : lo) + __shfl_xor_sync(kFull, b4 ? lo : hi, 16);
   }
   float k2[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float lo = k1[i];
     const float hi = (i + 3 < 5) ? k1[i + 3] : 0.f;
-    k2[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+    k2[i] = (b3 ? hi : lo) + __shfl_xor_sync(kFull, b3 ? lo : hi, 8);
   }
   float k3[2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const float lo = k2[i];
     const float hi = (i + 2 < 3) ? k2[i + 2] : 0.f;
-    k3[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+    k3[i] = (b2 ? hi : lo) + __shfl_xor_sync(kFull, b2 ? lo : hi, 4);
   }
-  const float k4 = (b1 ? k3[1] : k3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? k3[0] : k3[1], 2);
-  return k4 + __shfl_xor_sync(0xffffffffu, k4, 1);
+  const float k4 = (b1 ? k3[1] : k3[0]) + __shfl_xor_sync(kFull, b1 ? k3[0] : k3[1], 2);
+  return k4 + __shfl_xor_sync(kFull, k4, 1);
 }
 
 __device__ __forceinline__ int transpose_slot(int lane) {
@@ -215,14 +272,14 @@ struct PixelBwd {
   bool done;
 };
 
-__device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, int x, int y, int W, int H, int fmt,
-                                               const void* state, const uint32_t* last_in,
-                                               const float* dLdC) {
+__device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, int y, int W,
+                                               int fmt, const void* state,
+                                               const uint32_t* last_in, const float* dLdC) {
   p.Cp0 = p.Cp1 = p.Cp2 = 0.f;
   p.g0 = p.g1 = p.g2 = 0.f;
   p.T = 1.f;
   p.end = 0;
-  if (x < W && y < H) {
+  if (valid) {
     const size_t pix = (size_t)y * W + x;
     const float4 st = load_state(state, fmt, pix);
     p.Cp0 = st.x; p.Cp1 = st.y; p.Cp2 = st.z;
@@ -271,147 +328,143 @@ __device__ __forceinline__ void grad_fragment(PixelBwd& p, float q, float y1, fl
   v[4] += wz1 * z1;
 }
 
+__device__ __forceinline__ void red_add9(float* dst, const float v[9]) {
+  red_add_v4(dst, v[0], v[1], v[2], v[3]);
+  red_add_v4(dst + 4, v[4], v[5], v[6], v[7]);
+  red_add_v4(dst + 8, v[8], 0.f, 0.f, 0.f);
+}
+
+// part: this warp's 32 x 12 partial sums (slots 9..11 stay zero).
+template <int NPX, int MODE>
+__device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
+                                         const SplatRec* __restrict__ rec,
+                                         const uint32_t* __restrict__ pair_ranks, uint2 range,
+                                         int x0, int y0, int lane, int W, int H, float t_cull,
+                                         int fmt, const void* state, const uint32_t* last_in,
+                                         const float* dLdC, float* g2d, int threshold) {
+  constexpr int kCols = NPX == 2 ? 16 : 8;
+  const int x = x0 + lane % kCols;
+  const int ya = y0 + lane / kCols, yb = ya + 2;
+  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
+  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
+  const int tslot = transpose_slot(lane);
+  PixelBwd pa, pb;
+  load_pixel_bwd(pa, x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
+  if (NPX == 2) {
+    load_pixel_bwd(pb, x < W && yb < H, x, yb, W, fmt, state, last_in, dLdC);
+  } else {
+    pb.Cp0 = pb.Cp1 = pb.Cp2 = 0.f;
+    pb.g0 = pb.g1 = pb.g2 = 0.f;
+    pb.T = 1.f;
+    pb.end = 0u;
+    pb.done = true;
+  }
+  // depth ranks >= this contribute nowhere in the footprint
+  const uint32_t warp_end = __reduce_max_sync(kFull, max(pa.end, pb.end));
+
+  const uint32_t beg = range.x, end = warp_end > 0u ? range.y : range.x;
+  if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
+  int slot = 0;
+  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kStages - 1)) {
+    const uint32_t ip = gs + 32u * kStages + lane;
+    const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
+    cp_async_wait_group<kStages - 1>();
+    __syncwarp();
+    if (__all_sync(kFull, pa.done && pb.done)) break;
+    if (R.rank[slot][0] >= warp_end) break;   // ranks ascend along the list
+    const uint32_t cnt = min(32u, end - gs);
+    uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
+                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
+                                                       (float)(kCols - 1), 3.f));
+    uint32_t reduced = 0u;   // candidates whose warp sums wait in `part`
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const uint32_t rank = R.rank[slot][j];
+      float v[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = 0.f;
+      bool frag = false;
+      if (!(pa.done && pb.done)) {
+        const float4 a = R.a[slot][j];
+        const float4 b = R.b[slot][j];
+        float y1a, y2a, y1b = 0.f, y2b = 0.f, qb = 0.f;
+        const float qa = frag_q(px, pya, a, b, y1a, y2a);
+        if (NPX == 2) qb = frag_q(px, pyb, a, b, y1b, y2b);
+        if (rank >= pa.end) pa.done = true;   // past this pixel's last fragment
+        if (rank >= pb.end) pb.done = true;
+        const bool ha = !pa.done && qa <= b.y;
+        const bool hb = NPX == 2 && !pb.done && qb <= b.y;
+        if (ha || hb) {
+          const float4 c = R.c[slot][j];
+          frag = true;
+          if (ha) grad_fragment(pa, qa, y1a, y2a, a, b, c, t_cull, v);
+          if (NPX == 2 && hb) grad_fragment(pb, qb, y1b, y2b, a, b, c, t_cull, v);
+        }
+      }
+      if (MODE == GS_REDUCE_NAIVE) {
+        if (frag) red_add9(g2d + (size_t)rank * 12, v);
+      } else {
+        const uint32_t active = __ballot_sync(kFull, frag);
+        if (active != 0u) {
+          if (__popc(active) < threshold) {   // few lanes: add directly (Sec. 3.2.4)
+            if (frag) red_add9(g2d + (size_t)rank * 12, v);
+          } else {
+            const float tot = warp_transpose_reduce9(v, lane);
+            if (tslot >= 0) part[j][tslot] = tot;
+            reduced |= 1u << j;
+          }
+        }
+      }
+    }
+    if (MODE != GS_REDUCE_NAIVE && reduced) {
+      __syncwarp();
+      if ((reduced >> lane) & 1u) {   // lane j adds candidate j's totals
+        const float4* p = reinterpret_cast<const float4*>(part[lane]);
+        float* gdst = g2d + (size_t)R.rank[slot][lane] * 12;
+        const float4 p0 = p[0], p1 = p[1], p2 = p[2];
+        red_add_v4(gdst, p0.x, p0.y, p0.z, p0.w);
+        red_add_v4(gdst + 4, p1.x, p1.y, p1.z, p1.w);
+        red_add_v4(gdst + 8, p2.x, p2.y, p2.z, p2.w);
+      }
+    }
+    __syncwarp();   // every lane is done with the slot and `part` before they are reused
+    ring_issue(R, slot, rec, ip, end, rk_next, lane);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ items,
+    const Header* __restrict__ hdr, uint32_t* __restrict__ next,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, const void* __restrict__ state, const uint32_t* __restrict__ last_in,
     const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold) {
-  __shared__ Stage stg[2];
-  __shared__ __align__(16) float s_part[32][kWarps][12];
-  __shared__ uint32_t s_mask[kWarps];
-  __shared__ uint32_t s_end;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t tile = order[blockIdx.x];   // longest lists first
-  const int bx = tile % gw, by = tile / gw;
-  const int x = bx * kBlock + (lane & 15);
-  const int ya = by * kBlock + 4 * warp + (lane >> 4), yb = ya + 2;
-  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
-  const float xs = (float)(bx * kBlock) + 0.5f, ys = (float)(by * kBlock + 4 * warp) + 0.5f;
-  const uint2 range = ranges[tile];
-  const int slot = transpose_slot(lane);
-
-  PixelBwd pa, pb;
-  load_pixel_bwd(pa, x, ya, W, H, fmt, state, last_in, dLdC);
-  load_pixel_bwd(pb, x, yb, W, H, fmt, state, last_in, dLdC);
-  if (tid == 0) s_end = 0;
+  __shared__ WarpRing rings[kWarps];
+  __shared__ __align__(16) float s_part[kWarps][32][12];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpRing& R = rings[warp];
+  float (*part)[12] = s_part[warp];
   // padding slots 9..11 of the partial sums stay zero
-  for (int i = tid; i < 32 * kWarps; i += kThreads) {
-    float* p = &s_part[0][0][0] + i * 12;
-    p[9] = 0.f; p[10] = 0.f; p[11] = 0.f;
+  part[lane][9] = 0.f;
+  part[lane][10] = 0.f;
+  part[lane][11] = 0.f;
+  __syncwarp();
+  const uint32_t n_items = hdr->n_items;
+  for (uint32_t idx = next_item(next, lane); idx < n_items; idx = next_item(next, lane)) {
+    int block, x0, y0;
+    bool fine;
+    item_origin(items[idx], gw, block, x0, y0, fine);
+    const uint2 range = ranges[block];
+    if (fine)
+      bwd_item<1, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+                        last_in, dLdC, g2d, threshold);
+    else
+      bwd_item<2, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+                        last_in, dLdC, g2d, threshold);
   }
-  __syncthreads();
-  const uint32_t mine = max(pa.end, pb.end);
-  if (mine) atomicMax(&s_end, mine);
-  __syncthreads();
-  const uint32_t block_end = s_end;  // depth ranks >= this contribute nowhere in the block
-
-  uint32_t rk[kRecPerThread];
-  load_ranks(pair_ranks, range.x, range.y, rk);
-  if (range.x < range.y) stage_issue(stg[0], rec, range.x, range.y, rk);
-  load_ranks(pair_ranks, range.x + kBatch, range.y, rk);
-  int cur = 0;
-  for (uint32_t s = range.x; s < range.y; s += kBatch, cur ^= 1) {
-    cp_async_wait_all();
-    if (__syncthreads_and(pa.done && pb.done)) break;
-    const Stage& S = stg[cur];
-    if (S.rank[0] >= block_end) break;   // uniform: ranks ascend within the block
-    if (s + kBatch < range.y) {
-      stage_issue(stg[cur ^ 1], rec, s + kBatch, range.y, rk);
-      load_ranks(pair_ranks, s + 2 * kBatch, range.y, rk);
-    }
-    const int cnt = min((uint32_t)kBatch, range.y - s);
-    for (int k = 0; k * 32 < cnt; ++k) {
-      const int jt = k * 32 + lane;
-      uint32_t m = __ballot_sync(0xffffffffu,
-                                 jt < cnt && rect_may_hit(S.a[jt], S.b[jt], xs, ys, 15.f, 3.f));
-      if (__all_sync(0xffffffffu, pa.done && pb.done)) m = 0u;
-      if (MODE != GS_REDUCE_NAIVE && lane == 0) s_mask[warp] = m;
-      while (m) {
-        const int jj = __ffs(m) - 1;
-        m &= m - 1u;
-        const int j = k * 32 + jj;
-        const uint32_t rank = S.rank[j];
-        float v[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) v[q] = 0.f;
-        bool frag = false;
-        if (!(pa.done && pb.done)) {
-          const float4 a = S.a[j];
-          const float4 b = S.b[j];
-          float y1a, y2a, y1b, y2b;
-          const float qa = frag_q(px, pya, a, b, y1a, y2a);
-          const float qb = frag_q(px, pyb, a, b, y1b, y2b);
-          if (rank >= pa.end) pa.done = true;   // past this pixel's last fragment
-          if (rank >= pb.end) pb.done = true;
-          const bool ha = !pa.done && qa <= b.y;
-          const bool hb = !pb.done && qb <= b.y;
-          if (ha || hb) {
-            const float4 c = S.c[j];
-            frag = true;
-            if (ha) grad_fragment(pa, qa, y1a, y2a, a, b, c, t_cull, v);
-            if (hb) grad_fragment(pb, qb, y1b, y2b, a, b, c, t_cull, v);
-          }
-        }
-        float* gdst = g2d + (size_t)rank * 12;
-        if (MODE == GS_REDUCE_NAIVE) {
-          if (frag) {
-            red_add_v4(gdst, v[0], v[1], v[2], v[3]);
-            red_add_v4(gdst + 4, v[4], v[5], v[6], v[7]);
-            red_add_v4(gdst + 8, v[8], 0.f, 0.f, 0.f);
-          }
-        } else {
-          const uint32_t active = __ballot_sync(0xffffffffu, frag);
-          const bool reduce = active != 0u && __popc(active) >= threshold;
-          float tot = 0.f;
-          if (active != 0u && !reduce) {    // few lanes: add directly (Sec. 3.2.4)
-            if (frag) {
-              red_add_v4(gdst, v[0], v[1], v[2], v[3]);
-              red_add_v4(gdst + 4, v[4], v[5], v[6], v[7]);
-              red_add_v4(gdst + 8, v[8], 0.f, 0.f, 0.f);
-            }
-          } else if (reduce) {
-            tot = warp_transpose_reduce9(v, lane);
-          }
-          if (slot >= 0) s_part[jj][warp][slot] = tot;
-        }
-      }
-      if (MODE != GS_REDUCE_NAIVE) {
-        __syncthreads();
-        if (MODE == GS_REDUCE_BLOCK) {
-          // one thread per (splat, float4 group): sum the warps that looked at it
-          if (tid < 32 * 3) {
-            const int jj = tid / 3, q = tid % 3;
-            if (k * 32 + jj < cnt) {
-              float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-              for (int w = 0; w < kWarps; ++w) {
-                if ((s_mask[w] >> jj) & 1u) {
-                  const float4 p = *reinterpret_cast<const float4*>(&s_part[jj][w][4 * q]);
-                  acc.x += p.x; acc.y += p.y; acc.z += p.z; acc.w += p.w;
-                }
-              }
-              if (acc.x != 0.f || acc.y != 0.f || acc.z != 0.f || acc.w != 0.f)
-                red_add_v4(g2d + (size_t)S.rank[k * 32 + jj] * 12 + 4 * q, acc.x, acc.y, acc.z,
-                           acc.w);
-            }
-          }
-        } else {
-          // GS_REDUCE_WARP: each warp adds its own partial sums
-          if ((s_mask[warp] >> lane) & 1u) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              const float4 p = *reinterpret_cast<const float4*>(&s_part[lane][warp][4 * q]);
-              if (p.x != 0.f || p.y != 0.f || p.z != 0.f || p.w != 0.f)
-                red_add_v4(g2d + (size_t)S.rank[k * 32 + lane] * 12 + 4 * q, p.x, p.y, p.z, p.w);
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-  }
-  cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -437,7 +490,7 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ img
     if (grad) grad[i] = g;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -447,32 +500,54 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ img
   }
 }
 
-cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* order, const uint32_t* pair_ranks,
-                              const SplatRec* rec, int W, int H, int gw, int gh, float t_cull,
-                              int fmt, float* image, void* state, uint32_t* last,
-                              uint32_t* ncontrib, cudaStream_t st) {
-  const int blocks = gw * gh;
-  if (blocks == 0) return cudaSuccess;
-  raster_fwd_kernel<<<blocks, kThreads, 0, st>>>(ranges, order, pair_ranks, rec, W, H, gw, t_cull,
-                                                 fmt, image, state, last, ncontrib);
+namespace {
+// Resident CTAs per SM of `kernel` at kThreads.
+template <typename K>
+int resident_per_sm(K kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm;
+}
+}  // namespace
+
+cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const Header* hdr,
+                              uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
+                              int W, int H, int gw, int gh, float t_cull, int fmt, float* image,
+                              void* state, uint32_t* last, uint32_t* ncontrib, int num_sms,
+                              cudaStream_t st) {
+  if (gw * gh == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  static const int per_sm = resident_per_sm(raster_fwd_kernel);
+  const int grid = per_sm * num_sms;
+  raster_fwd_kernel<<<grid, kThreads, 0, st>>>(ranges, items, hdr, next, pair_ranks, rec, W, H, gw,
+                                               t_cull, fmt, image, state, last, ncontrib);
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* order, const uint32_t* pair_ranks,
-                              const SplatRec* rec, int W, int H, int gw, int gh, float t_cull,
-                              int fmt, const void* state, const uint32_t* last, const float* dLdC,
-                              float* g2d, int mode, int threshold, cudaStream_t st) {
-  const int blocks = gw * gh;
-  if (blocks == 0) return cudaSuccess;
-  if (mode == GS_REDUCE_NAIVE)
-    raster_bwd_kernel<GS_REDUCE_NAIVE><<<blocks, kThreads, 0, st>>>(
-        ranges, order, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d, threshold);
-  else if (mode == GS_REDUCE_WARP)
-    raster_bwd_kernel<GS_REDUCE_WARP><<<blocks, kThreads, 0, st>>>(
-        ranges, order, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d, threshold);
-  else
-    raster_bwd_kernel<GS_REDUCE_BLOCK><<<blocks, kThreads, 0, st>>>(
-        ranges, order, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d, threshold);
+cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* items, const Header* hdr,
+                              uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
+                              int W, int H, int gw, int gh, float t_cull, int fmt,
+                              const void* state, const uint32_t* last, const float* dLdC,
+                              float* g2d, int mode, int threshold, int num_sms, cudaStream_t st) {
+  if (gw * gh == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  if (mode == GS_REDUCE_NAIVE) {
+    static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_NAIVE>);
+    const int grid = per_sm * num_sms;
+    raster_bwd_kernel<GS_REDUCE_NAIVE><<<grid, kThreads, 0, st>>>(
+        ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
+        threshold);
+  } else {
+    static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_WARP>);
+    const int grid = per_sm * num_sms;
+    raster_bwd_kernel<GS_REDUCE_WARP><<<grid, kThreads, 0, st>>>(
+        ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
+        threshold);
+  }
   return cudaGetLastError();
 }
 

@@ -292,7 +292,7 @@ def test_backward_dense_with_t_culling():
     _check_backward(scene_np, cam, gs.RasterOpts(sh_degree=1, t_cull=1e-2), g)
 
 
-@pytest.mark.parametrize("mode,thr", [("warp", 0), ("naive", 0), ("block", 8), ("block", 33)])
+@pytest.mark.parametrize("mode,thr", [("naive", 0), ("warp", 8), ("warp", 33)])
 def test_reduction_modes_agree(mode, thr):
     """The reduction is exactly a sum: every mode gives the same per-splat
     accumulators up to FP32 reassociation."""
@@ -300,12 +300,12 @@ def test_reduction_modes_agree(mode, thr):
     cam = syn.look_at((0.0, 0.0, -3.5), (0.0, 0.0, 0.0), 50.0, 120, 90)
     g = syn.uniform_image(cam.height, cam.width, seed=62, lo=-1.0, hi=1.0)
     acc = {}
-    for m, x in (("block", 0), (mode, thr)):
+    for m, x in (("warp", 0), (mode, thr)):
         opts = gs.RasterOpts(reduce_mode=m, reduce_threshold=x)
         scene, ws, out, grads = run_forward_backward(scene_np, cam, opts, g)
         V = gs.read_counters(ws)["visible"]
         acc[(m, x)] = (gs.copy_array(ws, gs._lib.GS_ARRAY_GRAD2D, V).cpu().numpy().astype(np.float64), grads)
-    a, ga = acc[("block", 0)]
+    a, ga = acc[("warp", 0)]
     b, gb = acc[(mode, thr)]
     scale = np.abs(a).max(axis=0) + 1e-30
     assert np.max(np.abs(a - b) / scale) < 1e-5
@@ -396,3 +396,70 @@ def test_reduced_precision_state(fmt, img_tol, grad_tol):
     assert worst_img <= img_tol
     for k in GROUPS:
         assert worst[k] <= grad_tol, f"{fmt} {k}: {worst[k]:.3e}"
+
+
+# ---------------------------------------------------------------------------
+# Footprints of the raster work items
+# ---------------------------------------------------------------------------
+
+def _split_scenes():
+    """A pile of small splats (most candidates hit two or three of a warp's
+    pixels), a dense scene of larger splats, and a ragged image."""
+    small = syn.cube_scene(6000, seed=71, sh_degree=1, log_scale_mean=-4.2, log_scale_std=0.4)
+    cam_s = syn.look_at((0.0, 0.0, -2.6), (0.0, 0.0, 0.0), 50.0, 160, 112)
+    dense = syn.cube_scene(2500, seed=72, sh_degree=0, log_scale_mean=-2.2)
+    cam_d = syn.look_at((0.0, 0.0, -3.5), (0.0, 0.0, 0.0), 50.0, 128, 96)
+    ragged = syn.cube_scene(1500, seed=73, sh_degree=2, log_scale_mean=-3.3)
+    cam_r = syn.look_at((0.3, -0.2, -3.0), (0.0, 0.0, 0.0), 55.0, 91, 57)
+    return [(small, cam_s), (dense, cam_d), (ragged, cam_r)]
+
+
+# split thresholds: every block in 8x4 cells, the default mix, every block in 16x4 bands
+SPLITS = (1, 0, 1 << 30)
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_footprints_give_identical_images(which):
+    scene_np, cam = _split_scenes()[which]
+    outs = {}
+    for split in SPLITS:
+        _, _, out = run_forward(scene_np, cam, gs.RasterOpts(sh_degree=scene_np.sh_degree,
+                                                             split_threshold=split))
+        outs[split] = out
+    ref = outs[1 << 30]
+    assert int(ref["n_contrib"].sum()) > 0
+    for split in SPLITS[:2]:
+        for key in ("image", "state", "last", "n_contrib"):
+            assert torch.equal(outs[split][key], ref[key]), (split, key)
+
+
+@pytest.mark.parametrize("split", [1, 1 << 30])
+@pytest.mark.parametrize("mode", ["warp", "naive"])
+def test_footprints_backward_match_oracle(split, mode):
+    scene_np, cam = _split_scenes()[0]
+    g = syn.uniform_image(cam.height, cam.width, seed=74, lo=-1.0, hi=1.0)
+    opts = gs.RasterOpts(sh_degree=scene_np.sh_degree, split_threshold=split, reduce_mode=mode)
+    _check_backward(scene_np, cam, opts, g)
+
+
+def test_footprints_backward_agree():
+    """8x4 cells and 16x4 bands give the same per-splat accumulators up to FP32
+    summation order."""
+    scene_np, cam = _split_scenes()[1]
+    g = syn.uniform_image(cam.height, cam.width, seed=76, lo=-1.0, hi=1.0)
+    acc = []
+    for split in (1, 1 << 30):
+        o = gs.RasterOpts(sh_degree=scene_np.sh_degree, split_threshold=split)
+        scene, ws, out, grads = run_forward_backward(scene_np, cam, o, g)
+        V = gs.read_counters(ws)["visible"]
+        acc.append(gs.copy_array(ws, gs._lib.GS_ARRAY_GRAD2D, V).cpu().numpy().astype(np.float64))
+    scale = np.abs(acc[1]).max(axis=0) + 1e-30
+    assert np.max(np.abs(acc[0] - acc[1]) / scale) < 1e-5
+
+
+def test_footprints_with_t_culling_and_ragged_image():
+    scene_np, cam = _split_scenes()[2]
+    g = syn.uniform_image(cam.height, cam.width, seed=75, lo=-1.0, hi=1.0)
+    for split in (1, 0):
+        _check_backward(scene_np, cam, gs.RasterOpts(sh_degree=scene_np.sh_degree, t_cull=1e-2,
+                                                     split_threshold=split), g)
