@@ -35,7 +35,7 @@ WORKLOAD = "mipnerf360-shaped synthetic scene, 3.0M splats SH3, 1256x828, L1 los
 N_SPLATS = 3_000_000
 STAGES = ("project", "sort", "bin", "blend_fwd", "loss", "blend_bwd", "project_bwd")
 KERNELS_PER_STAGE = {"project": 1, "sort": 4, "bin": None, "blend_fwd": 1, "loss": 1,
-                     "blend_bwd": 1, "project_bwd": 1}   # bin: 2 + pair-sort passes
+                     "blend_bwd": 2, "project_bwd": 1}   # bin: 2 + pair-sort passes
 # Nominal FP32 rate (SM count x FP32 lanes x 2 flop x max SM clock): raster stages are
 # plain FP32 ALU work, for which the measured peaks carry no figure.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -227,7 +227,8 @@ def run_ours(args, rank, world, local_rank):
     P_live = int((rg[:, 1] - rg[:, 0]).sum().item())
     npix = H * W
     passes = ws.c.pair_passes
-    kernels_per_step = 1 + 4 + (2 + passes + 2) + 1 + 1 + 1 + 1   # bin: count, emit, passes, ranges, order
+    # bin: count, emit, pair-sort passes, ranges, item order; blend_bwd: item reorder + raster
+    kernels_per_step = 1 + 4 + (2 + passes + 2) + 1 + 1 + 2 + 1
     K_sh = 16
 
     # algorithmic bytes (HBM-bound stages) and flops (raster stages) per launch

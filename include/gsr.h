@@ -82,7 +82,7 @@ typedef struct gs_camera {
   float znear;
 } gs_camera;
 
-#define GS_SPLIT_THRESHOLD_DEFAULT 2048
+#define GS_SPLIT_THRESHOLD_DEFAULT 1024
 
 typedef struct gs_raster_opts {
   int32_t state_format;     /* GS_STATE_* */

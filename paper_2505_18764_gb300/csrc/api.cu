@@ -29,13 +29,13 @@ cudaError_t launch_bin(const uint32_t*, const SplatRec*, const uint2*, SplatRec*
                        uint32_t*, uint32_t, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, int, cudaStream_t);
 cudaError_t launch_block_order(const uint2*, int, uint32_t, uint32_t*, Header*, cudaStream_t);
-cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint32_t*,
+cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint32_t*, uint32_t*,
                               const uint32_t*, const SplatRec*, int, int, int, int, float, int,
                               float*, void*, uint32_t*, uint32_t*, int, cudaStream_t);
-cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const Header*, uint32_t*,
-                              const uint32_t*, const SplatRec*, int, int, int, int, float, int,
-                              const void*, const uint32_t*, const float*, float*, int, int, int,
-                              cudaStream_t);
+cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, uint32_t*,
+                              const Header*, uint32_t*, const uint32_t*, const SplatRec*, int, int,
+                              int, int, float, int, const void*, const uint32_t*, const float*,
+                              float*, int, int, int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
                         cudaStream_t);
 size_t sort_tiles(size_t n);
@@ -100,6 +100,8 @@ enum Slot {
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
   L_ORDER,       // [8 blocks_cap] u32 raster work items (warp footprints), longest lists first
+  L_ITEM_COST,   // [8 blocks_cap] u32 cost of each item in the last forward raster
+  L_BWD_ITEMS,   // [8 blocks_cap] u32 the items again, costliest first, for the backward raster
   L_END
 };
 
@@ -136,7 +138,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
-  sz[L_ORDER] = blocks * 8 * 4;
+  sz[L_ORDER] = sz[L_ITEM_COST] = sz[L_BWD_ITEMS] = blocks * 8 * 4;
   size_t o = 0;
   for (int i = 0; i < L_END; ++i) {
     off[i] = o;
@@ -363,7 +365,8 @@ int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
   const int fin = ws->pair_passes & 1;
   Header* hdr = at<Header>(ws, L_HDR);
   GS_CUDA(launch_raster_fwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER), hdr,
-                            &hdr->raster_next[0], at<uint32_t>(ws, fin ? L_PVB : L_PVA),
+                            &hdr->raster_next[0], at<uint32_t>(ws, L_ITEM_COST),
+                            at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, image, state, last, n_contrib,
                             num_sms(), reinterpret_cast<cudaStream_t>(stream)),
@@ -395,7 +398,8 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
   Header* hdr = at<Header>(ws, L_HDR);
-  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER), hdr,
+  GS_CUDA(launch_raster_bwd(at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_ORDER),
+                            at<uint32_t>(ws, L_ITEM_COST), at<uint32_t>(ws, L_BWD_ITEMS), hdr,
                             &hdr->raster_next[1], at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, state, last, dL_dimage,

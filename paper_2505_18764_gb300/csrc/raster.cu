@@ -9,8 +9,10 @@
 // list is long, into eight 8x4 footprints with one pixel per lane: a block
 // under a pile of small splats is then walked by twice as many warps, each
 // meeting fewer candidates, instead of setting the launch time on its own.
-// Persistent CTAs take items from a counter in the order the binning wrote
-// them (longest lists first).
+// Persistent CTAs take items from a counter: the forward in the order the
+// binning wrote them (longest lists first), the backward costliest first by
+// the forward's measured time per item (fragment density, not list length,
+// decides most of it).
 //
 // That is the CUDA counterpart of the paper's ordered fragment processing: a
 // pixel belongs to one lane, which meets the block's splats in depth order, so
@@ -201,7 +203,7 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
 
 __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ items,
-    const Header* __restrict__ hdr, uint32_t* __restrict__ next,
+    const Header* __restrict__ hdr, uint32_t* __restrict__ next, uint32_t* __restrict__ item_cost,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, float* __restrict__ image, void* __restrict__ state,
     uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib) {
@@ -214,12 +216,14 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     bool fine;
     item_origin(items[idx], gw, block, x0, y0, fine);
     const uint2 range = ranges[block];
+    const long long t0 = clock64();
     if (fine)
       fwd_item<1>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
                   last_out, ncontrib);
     else
       fwd_item<2>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
                   last_out, ncontrib);
+    if (lane == 0) item_cost[idx] = (uint32_t)min(clock64() - t0, (long long)0xFFFFFFFF);
   }
 }
 
@@ -467,6 +471,41 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   }
 }
 
+// The forward's items reordered costliest first: a counting sort by
+// log-bucket of the measured cost (4 buckets per octave).  Any cost values
+// give a permutation of the items, so stale costs only cost time.
+constexpr int kCostBuckets = 128;
+
+__device__ __forceinline__ int cost_bucket(uint32_t c) {
+  if (c == 0) return kCostBuckets - 1;
+  const int lg = 31 - __clz(c);
+  const int frac = lg >= 2 ? (int)((c >> (lg - 2)) & 3) : 0;
+  return kCostBuckets - 2 - min(lg * 4 + frac, kCostBuckets - 2);
+}
+
+__global__ void __launch_bounds__(1024) item_order_kernel(const uint32_t* __restrict__ items,
+                                                         const uint32_t* __restrict__ cost,
+                                                         const Header* __restrict__ hdr,
+                                                         uint32_t* __restrict__ out) {
+  __shared__ uint32_t s_cnt[kCostBuckets];
+  const uint32_t n = hdr->n_items;
+  for (int i = threadIdx.x; i < kCostBuckets; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[cost_bucket(cost[i])], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kCostBuckets; ++i) {
+      const uint32_t c = s_cnt[i];
+      s_cnt[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+    out[atomicAdd(&s_cnt[cost_bucket(cost[i])], 1u)] = items[i];
+}
+
 // ---------------------------------------------------------------------------
 // Summed L1 / L2 image loss and its gradient.
 // ---------------------------------------------------------------------------
@@ -513,7 +552,8 @@ int resident_per_sm(K kernel) {
 }  // namespace
 
 cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const Header* hdr,
-                              uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
+                              uint32_t* next, uint32_t* item_cost, const uint32_t* pair_ranks,
+                              const SplatRec* rec,
                               int W, int H, int gw, int gh, float t_cull, int fmt, float* image,
                               void* state, uint32_t* last, uint32_t* ncontrib, int num_sms,
                               cudaStream_t st) {
@@ -522,18 +562,22 @@ cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const 
   if (e != cudaSuccess) return e;
   static const int per_sm = resident_per_sm(raster_fwd_kernel);
   const int grid = per_sm * num_sms;
-  raster_fwd_kernel<<<grid, kThreads, 0, st>>>(ranges, items, hdr, next, pair_ranks, rec, W, H, gw,
-                                               t_cull, fmt, image, state, last, ncontrib);
+  raster_fwd_kernel<<<grid, kThreads, 0, st>>>(ranges, items, hdr, next, item_cost, pair_ranks, rec,
+                                               W, H, gw, t_cull, fmt, image, state, last, ncontrib);
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* items, const Header* hdr,
+cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
+                              const uint32_t* item_cost, uint32_t* items, const Header* hdr,
                               uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
                               int W, int H, int gw, int gh, float t_cull, int fmt,
                               const void* state, const uint32_t* last, const float* dLdC,
                               float* g2d, int mode, int threshold, int num_sms, cudaStream_t st) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  item_order_kernel<<<1, 1024, 0, st>>>(fwd_items, item_cost, hdr, items);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mode == GS_REDUCE_NAIVE) {
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_NAIVE>);

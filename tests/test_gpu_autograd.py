@@ -100,8 +100,11 @@ def test_backward_after_workspace_reuse():
     pc = _params(scene_np)
     img_c = ga.render(*pc, cams[0], opts, ws)
     (img_c * g).sum().backward()
+    # the per-splat sums are atomic adds in an order that varies run to run:
+    # equal up to FP32 reassociation
     for x, y in zip(pa, pc):
-        torch.testing.assert_close(x.grad, y.grad, rtol=1e-5, atol=1e-6)
+        err = (x.grad - y.grad).norm() / y.grad.norm().clamp_min(1e-30)
+        assert err < 1e-5, float(err)
     assert torch.equal(img_a, img_c)
 
 
