@@ -62,7 +62,7 @@ enum {
 
 /* Per-splat gradient reduction in the backward raster (Sec. 3.2).  The raster
  * kernels give each warp a footprint of 64 pixels (16x4) or, in blocks with
- * long splat lists, 32 pixels (8x4). */
+ * long splat lists, 32 (8x4) or 16 (4x4). */
 enum {
   GS_REDUCE_WARP = 0, /* transpose-reduce over the warp: one vector-atomic triple per (splat, footprint) */
   GS_REDUCE_NAIVE = 1 /* one vector-atomic triple per fragment (the paper's 1x baseline) */
@@ -82,7 +82,7 @@ typedef struct gs_camera {
   float znear;
 } gs_camera;
 
-#define GS_SPLIT_THRESHOLD_DEFAULT 1024
+#define GS_SPLIT_THRESHOLD_DEFAULT 1536
 
 typedef struct gs_raster_opts {
   int32_t state_format;     /* GS_STATE_* */
@@ -90,10 +90,11 @@ typedef struct gs_raster_opts {
   int32_t reduce_threshold; /* X of Sec. 3.2.4: warps with fewer active lanes add directly */
   int32_t sh_degree;        /* 0..3 */
   float t_cull;             /* skip fragment i iff T_i < t_cull (Procedure 1); 0 disables */
-  int32_t split_threshold;  /* blocks whose splat list has at least this many entries are
-                               walked by eight warps (8x4 pixels, one per lane) instead of four
-                               (16x4, two per lane); 0 = default (GS_SPLIT_THRESHOLD_DEFAULT),
-                               1 = every block.  Results do not depend on it. */
+  int32_t split_threshold;  /* a block whose splat list has at least this many entries is walked
+                               by eight warps (8x4 pixels, one per lane) instead of four (16x4,
+                               two per lane), from 8x this many by sixteen half-warps (4x4);
+                               0 = default (GS_SPLIT_THRESHOLD_DEFAULT).  Results do not depend
+                               on it. */
   int64_t pair_capacity;    /* (splat, 16x16 block) pairs the workspace holds; 0 = 16 per splat */
 } gs_raster_opts;
 

@@ -99,9 +99,9 @@ enum Slot {
   L_CHUNKS,      // [pair_cap / 2048 + 1] first depth rank of each emission chunk
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
-  L_ORDER,       // [8 blocks_cap] u32 raster work items (warp footprints), longest lists first
-  L_ITEM_COST,   // [8 blocks_cap] u32 cost of each item in the last forward raster
-  L_BWD_ITEMS,   // [8 blocks_cap] u32 the items again, costliest first, for the backward raster
+  L_ORDER,       // [16 blocks_cap] u32 raster work items (warp footprints), longest lists first
+  L_ITEM_COST,   // [16 blocks_cap] u32 cost of each item in the last forward raster
+  L_BWD_ITEMS,   // [16 blocks_cap] u32 the items again, costliest first, for the backward raster
   L_END
 };
 
@@ -138,7 +138,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
-  sz[L_ORDER] = sz[L_ITEM_COST] = sz[L_BWD_ITEMS] = blocks * 8 * 4;
+  sz[L_ORDER] = sz[L_ITEM_COST] = sz[L_BWD_ITEMS] = blocks * 16 * 4;
   size_t o = 0;
   for (int i = 0; i < L_END; ++i) {
     off[i] = o;

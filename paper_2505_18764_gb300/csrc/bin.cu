@@ -234,9 +234,14 @@ __device__ __forceinline__ int length_bucket(uint32_t len) {
 }
 
 // Raster work items, longest lists first: a counting sort of the blocks by
-// length bucket, each block writing its items contiguously (four 16x4 bands,
-// or eight 8x4 cells when its list has at least `split` entries; see
-// raster.cu for the encoding).  The item count goes to the header.
+// length bucket, each block writing its items contiguously: four 16x4 bands,
+// eight 8x4 cells when its list has at least `split` entries, sixteen 4x4
+// cells from 8 `split` entries on (raster.cu has the encoding).  The item
+// count goes to the header.
+__device__ __forceinline__ uint32_t block_items(uint32_t len, uint32_t split) {
+  return len >= 8u * (uint64_t)split ? 16u : (len >= split ? 8u : 4u);
+}
+
 __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restrict__ ranges,
                                                           int nblocks, uint32_t split,
                                                           uint32_t* __restrict__ items,
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restri
   __syncthreads();
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
     const uint32_t len = ranges[b].y - ranges[b].x;
-    atomicAdd(&s_cnt[length_bucket(len)], len >= split ? 8u : 4u);
+    atomicAdd(&s_cnt[length_bucket(len)], block_items(len, split));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -261,10 +266,10 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restri
   __syncthreads();
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
     const uint32_t len = ranges[b].y - ranges[b].x;
-    const bool fine = len >= split;
-    const uint32_t n = fine ? 8u : 4u;
+    const uint32_t n = block_items(len, split);
+    const uint32_t code0 = n == 16u ? 16u : (n == 8u ? 8u : 0u);
     const uint32_t pos = atomicAdd(&s_pos[length_bucket(len)], n);
-    for (uint32_t k = 0; k < n; ++k) items[pos + k] = ((uint32_t)b << 4) | (fine ? 8u + k : k);
+    for (uint32_t k = 0; k < n; ++k) items[pos + k] = ((uint32_t)b << 5) | (code0 + k);
   }
 }
 

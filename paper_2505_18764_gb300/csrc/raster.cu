@@ -6,9 +6,10 @@
 // private ring in shared memory (asynchronous copies, kStages groups in
 // flight), so warps never wait for one another.  A block is cut into four
 // 16x4 footprints with two pixels per lane (rows r and r + 2), or, when its
-// list is long, into eight 8x4 footprints with one pixel per lane: a block
-// under a pile of small splats is then walked by twice as many warps, each
-// meeting fewer candidates, instead of setting the launch time on its own.
+// list is long, into eight 8x4 footprints with one pixel per lane, or, when
+// it is very long, into sixteen 4x4 footprints on half a warp: a block under
+// a pile of small splats is then walked by more warps, each meeting fewer
+// candidates, instead of setting the launch time on its own.
 // Persistent CTAs take items from a counter: the forward in the order the
 // binning wrote them (longest lists first), the backward costliest first by
 // the forward's measured time per item (fragment density, not list length,
@@ -43,9 +44,10 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kStages = 4;                    // groups of 32 records in flight per warp
 constexpr unsigned kFull = 0xffffffffu;
 
-// Item encoding: block << 4 | code; code 0..3 = 16x4 band (two pixels per
-// lane), code 8..15 = 8x4 cell (one pixel per lane).
-constexpr uint32_t kFineCode = 8u;
+// Item encoding: block << 5 | code; code 0..3 = 16x4 band (two pixels per
+// lane), 8..15 = 8x4 cell (one pixel per lane), 16..31 = 4x4 cell (one pixel
+// on each of lanes 0..15).
+constexpr uint32_t kCell8Code = 8u, kCell4Code = 16u;
 
 struct WarpRing {
   float4 a[kStages][32];
@@ -90,20 +92,36 @@ __device__ __forceinline__ uint32_t next_item(uint32_t* counter, int lane) {
   return __shfl_sync(kFull, idx, 0);
 }
 
-__device__ __forceinline__ void item_origin(uint32_t it, int gw, int& block, int& x0, int& y0,
-                                            bool& fine) {
-  block = (int)(it >> 4);
-  const int code = (int)(it & 15u);
+// Block and top-left pixel of an item; returns the footprint width (16, 8 or 4).
+__device__ __forceinline__ int item_origin(uint32_t it, int gw, int& block, int& x0, int& y0) {
+  block = (int)(it >> 5);
+  const int code = (int)(it & 31u);
   const int bx = block % gw, by = block / gw;
-  fine = code >= (int)kFineCode;
-  if (!fine) {
-    x0 = bx * kBlock;
-    y0 = by * kBlock + 4 * code;
-  } else {
-    const int c = code - (int)kFineCode;
-    x0 = bx * kBlock + 8 * (c & 1);
-    y0 = by * kBlock + 4 * (c >> 1);
+  x0 = bx * kBlock;
+  y0 = by * kBlock;
+  if (code < (int)kCell8Code) {
+    y0 += 4 * code;
+    return 16;
   }
+  if (code < (int)kCell4Code) {
+    const int c = code - (int)kCell8Code;
+    x0 += 8 * (c & 1);
+    y0 += 4 * (c >> 1);
+    return 8;
+  }
+  const int c = code - (int)kCell4Code;
+  x0 += 4 * (c & 3);
+  y0 += 4 * (c >> 2);
+  return 4;
+}
+
+// This lane's pixels in a footprint COLS wide and 4 high: (x, ya) and, for
+// COLS = 16, (x, ya + 2); lanes beyond a 4x4 footprint own no pixel.
+template <int COLS>
+__device__ __forceinline__ void lane_pixels(int x0, int y0, int lane, int& x, int& ya, bool& own) {
+  x = x0 + lane % COLS;
+  ya = y0 + (COLS == 16 ? lane / 16 : lane / COLS);
+  own = COLS != 4 || lane < 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -142,20 +160,21 @@ __device__ __forceinline__ void write_fwd(const PixelFwd& p, int x, int y, int W
   if (ncontrib) ncontrib[pix] = p.n;
 }
 
-// One warp, one footprint: NPX = 2 for a 16x4 band (rows r, r + 2 per lane),
-// NPX = 1 for an 8x4 cell.
-template <int NPX>
+// One warp, one footprint COLS x 4 (two pixels per lane when COLS = 16).
+template <int COLS>
 __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict__ rec,
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
                                          int x0, int y0, int lane, int W, int H, float t_cull,
                                          int fmt, float* image, void* state, uint32_t* last_out,
                                          uint32_t* ncontrib) {
-  constexpr int kCols = NPX == 2 ? 16 : 8;
-  const int x = x0 + lane % kCols;
-  const int ya = y0 + lane / kCols, yb = ya + 2;
+  constexpr int NPX = COLS == 16 ? 2 : 1;
+  int x, ya;
+  bool own;
+  lane_pixels<COLS>(x0, y0, lane, x, ya, own);
+  const int yb = ya + 2;
   const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
-  PixelFwd pa{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(x < W && ya < H)};
+  PixelFwd pa{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(own && x < W && ya < H)};
   PixelFwd pb{1.f, 0.f, 0.f, 0.f, kNone, 0u, NPX == 1 || !(x < W && yb < H)};
 
   const uint32_t beg = range.x, end = range.y;
@@ -170,7 +189,7 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
     const uint32_t cnt = min(32u, end - gs);
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
-                                                       (float)(kCols - 1), 3.f));
+                                                       (float)(COLS - 1), 3.f));
     while (m) {
       const int j = __ffs(m) - 1;
       m &= m - 1u;
@@ -197,7 +216,7 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
   }
   cp_async_wait_all();
   __syncwarp();
-  write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
+  if (own) write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
   if (NPX == 2) write_fwd(pb, x, yb, W, H, fmt, image, state, last_out, ncontrib);
 }
 
@@ -213,15 +232,17 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
   const uint32_t n_items = hdr->n_items;
   for (uint32_t idx = next_item(next, lane); idx < n_items; idx = next_item(next, lane)) {
     int block, x0, y0;
-    bool fine;
-    item_origin(items[idx], gw, block, x0, y0, fine);
+    const int cols = item_origin(items[idx], gw, block, x0, y0);
     const uint2 range = ranges[block];
     const long long t0 = clock64();
-    if (fine)
-      fwd_item<1>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
+    if (cols == 16)
+      fwd_item<16>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
+                   last_out, ncontrib);
+    else if (cols == 8)
+      fwd_item<8>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
                   last_out, ncontrib);
     else
-      fwd_item<2>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
+      fwd_item<4>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
                   last_out, ncontrib);
     if (lane == 0) item_cost[idx] = (uint32_t)min(clock64() - t0, (long long)0xFFFFFFFF);
   }
@@ -339,21 +360,23 @@ __device__ __forceinline__ void red_add9(float* dst, const float v[9]) {
 }
 
 // part: this warp's 32 x 12 partial sums (slots 9..11 stay zero).
-template <int NPX, int MODE>
+template <int COLS, int MODE>
 __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
                                          const SplatRec* __restrict__ rec,
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
                                          int x0, int y0, int lane, int W, int H, float t_cull,
                                          int fmt, const void* state, const uint32_t* last_in,
                                          const float* dLdC, float* g2d, int threshold) {
-  constexpr int kCols = NPX == 2 ? 16 : 8;
-  const int x = x0 + lane % kCols;
-  const int ya = y0 + lane / kCols, yb = ya + 2;
+  constexpr int NPX = COLS == 16 ? 2 : 1;
+  int x, ya;
+  bool own;
+  lane_pixels<COLS>(x0, y0, lane, x, ya, own);
+  const int yb = ya + 2;
   const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
   const int tslot = transpose_slot(lane);
   PixelBwd pa, pb;
-  load_pixel_bwd(pa, x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
+  load_pixel_bwd(pa, own && x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
   if (NPX == 2) {
     load_pixel_bwd(pb, x < W && yb < H, x, yb, W, fmt, state, last_in, dLdC);
   } else {
@@ -379,7 +402,7 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
     const uint32_t cnt = min(32u, end - gs);
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
-                                                       (float)(kCols - 1), 3.f));
+                                                       (float)(COLS - 1), 3.f));
     uint32_t reduced = 0u;   // candidates whose warp sums wait in `part`
     while (m) {
       const int j = __ffs(m) - 1;
@@ -459,14 +482,16 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   const uint32_t n_items = hdr->n_items;
   for (uint32_t idx = next_item(next, lane); idx < n_items; idx = next_item(next, lane)) {
     int block, x0, y0;
-    bool fine;
-    item_origin(items[idx], gw, block, x0, y0, fine);
+    const int cols = item_origin(items[idx], gw, block, x0, y0);
     const uint2 range = ranges[block];
-    if (fine)
-      bwd_item<1, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+    if (cols == 16)
+      bwd_item<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+                         last_in, dLdC, g2d, threshold);
+    else if (cols == 8)
+      bwd_item<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
                         last_in, dLdC, g2d, threshold);
     else
-      bwd_item<2, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+      bwd_item<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
                         last_in, dLdC, g2d, threshold);
   }
 }

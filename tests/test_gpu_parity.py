@@ -414,8 +414,9 @@ def _split_scenes():
     return [(small, cam_s), (dense, cam_d), (ragged, cam_r)]
 
 
-# split thresholds: every block in 8x4 cells, the default mix, every block in 16x4 bands
-SPLITS = (1, 0, 1 << 30)
+# split thresholds: nearly every block in 4x4 cells; 16x4 bands, 8x4 and 4x4 cells mixed;
+# the default mix; every block in 16x4 bands
+SPLITS = (1, 48, 0, 1 << 30)
 
 
 @pytest.mark.parametrize("which", [0, 1, 2])
@@ -428,12 +429,12 @@ def test_footprints_give_identical_images(which):
         outs[split] = out
     ref = outs[1 << 30]
     assert int(ref["n_contrib"].sum()) > 0
-    for split in SPLITS[:2]:
+    for split in SPLITS[:3]:
         for key in ("image", "state", "last", "n_contrib"):
             assert torch.equal(outs[split][key], ref[key]), (split, key)
 
 
-@pytest.mark.parametrize("split", [1, 1 << 30])
+@pytest.mark.parametrize("split", [1, 48, 1 << 30])
 @pytest.mark.parametrize("mode", ["warp", "naive"])
 def test_footprints_backward_match_oracle(split, mode):
     scene_np, cam = _split_scenes()[0]
@@ -448,18 +449,19 @@ def test_footprints_backward_agree():
     scene_np, cam = _split_scenes()[1]
     g = syn.uniform_image(cam.height, cam.width, seed=76, lo=-1.0, hi=1.0)
     acc = []
-    for split in (1, 1 << 30):
+    for split in (1, 48, 1 << 30):
         o = gs.RasterOpts(sh_degree=scene_np.sh_degree, split_threshold=split)
         scene, ws, out, grads = run_forward_backward(scene_np, cam, o, g)
         V = gs.read_counters(ws)["visible"]
         acc.append(gs.copy_array(ws, gs._lib.GS_ARRAY_GRAD2D, V).cpu().numpy().astype(np.float64))
-    scale = np.abs(acc[1]).max(axis=0) + 1e-30
-    assert np.max(np.abs(acc[0] - acc[1]) / scale) < 1e-5
+    scale = np.abs(acc[-1]).max(axis=0) + 1e-30
+    for a in acc[:-1]:
+        assert np.max(np.abs(a - acc[-1]) / scale) < 1e-5
 
 
 def test_footprints_with_t_culling_and_ragged_image():
     scene_np, cam = _split_scenes()[2]
     g = syn.uniform_image(cam.height, cam.width, seed=75, lo=-1.0, hi=1.0)
-    for split in (1, 0):
+    for split in (1, 48, 0):
         _check_backward(scene_np, cam, gs.RasterOpts(sh_degree=scene_np.sh_degree, t_cull=1e-2,
                                                      split_threshold=split), g)
