@@ -83,11 +83,14 @@ typedef struct gs_camera {
 } gs_camera;
 
 #define GS_SPLIT_THRESHOLD_DEFAULT 1536
+#define GS_REDUCE_THRESHOLD_DEFAULT 16
 
 typedef struct gs_raster_opts {
   int32_t state_format;     /* GS_STATE_* */
   int32_t reduce_mode;      /* GS_REDUCE_* */
-  int32_t reduce_threshold; /* X of Sec. 3.2.4: warps with fewer active lanes add directly */
+  int32_t reduce_threshold; /* X of Sec. 3.2.4: a splat met by fewer than X lanes of a warp is
+                               added by those lanes directly; 0 = default
+                               (GS_REDUCE_THRESHOLD_DEFAULT), 1 = always reduce first */
   int32_t sh_degree;        /* 0..3 */
   float t_cull;             /* skip fragment i iff T_i < t_cull (Procedure 1); 0 disables */
   int32_t split_threshold;  /* a block whose splat list has at least this many entries is walked

@@ -158,6 +158,7 @@ int check_opts(const gs_raster_opts* o) {
   if (o->state_format < 0 || o->state_format > 3) return fail(GS_ERR_INVALID_ARG, "bad state_format %d", o->state_format);
   if (o->reduce_mode < 0 || o->reduce_mode > 1) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
   if (o->split_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad split_threshold %d", o->split_threshold);
+  if (o->reduce_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad reduce_threshold %d", o->reduce_threshold);
   if (o->sh_degree < 0 || o->sh_degree > kMaxShDegree) return fail(GS_ERR_INVALID_ARG, "bad sh_degree %d", o->sh_degree);
   if (!(o->t_cull >= 0.f && o->t_cull <= 1.f)) return fail(GS_ERR_INVALID_ARG, "t_cull must be in [0, 1]");
   if (o->pair_capacity < 0 || o->pair_capacity >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [0, 2^30)");
@@ -403,7 +404,9 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
                             &hdr->raster_next[1], at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, state, last, dL_dimage,
-                            at<float>(ws, L_G2D), opts->reduce_mode, opts->reduce_threshold,
+                            at<float>(ws, L_G2D), opts->reduce_mode,
+                            opts->reduce_threshold > 0 ? opts->reduce_threshold
+                                                       : GS_REDUCE_THRESHOLD_DEFAULT,
                             num_sms(), reinterpret_cast<cudaStream_t>(stream)),
           "raster backward kernel");
   return GS_OK;

@@ -93,34 +93,49 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
       if (w < warp) wbefore += v;
       total += v;
     }
-    // tile offset by decoupled look-back over lower tiles
-    if (tid == 0) {
+    // tile offset by decoupled look-back over lower tiles, 32 of them per round
+    // trip (lane l reads tile j - l)
+    if (warp == 0) {
       unsigned long long* my = scan_status + tile;
       unsigned long long excl = 0;
       const unsigned long long tot = min((unsigned long long)total, kBinCount);
       if (tile == 0) {
-        st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | tot);
+        if (lane == 0) st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | tot);
       } else {
-        st_relaxed64(my, ((unsigned long long)tag << 32) | kBinAgg | tot);
+        if (lane == 0) st_relaxed64(my, ((unsigned long long)tag << 32) | kBinAgg | tot);
         int64_t j = (int64_t)tile - 1;
         uint32_t spins = 0;
         while (j >= 0) {
-          const unsigned long long s = ld_relaxed64(scan_status + j);
-          const bool ready = (uint32_t)(s >> 32) == tag && (s & (3ull << 30)) != 0;
-          if (!ready) {
+          const int64_t t = j - lane;
+          const unsigned long long s = t >= 0 ? ld_relaxed64(scan_status + t) : 0ull;
+          const bool ready = t >= 0 && (uint32_t)(s >> 32) == tag && (s & (3ull << 30)) != 0;
+          const uint32_t waiting = __ballot_sync(0xffffffffu, t >= 0 && !ready);
+          const uint32_t prefix = __ballot_sync(0xffffffffu, ready && (s & (3ull << 30)) == kBinPre);
+          const int first_wait = waiting ? __ffs(waiting) - 1 : 32;
+          const int first_pre = prefix ? __ffs(prefix) - 1 : 32;
+          // lanes before the first unpublished word are consumed; a prefix ends the walk
+          const int take = first_pre < first_wait ? first_pre + 1 : first_wait;
+          unsigned long long c = (lane < take && t >= 0) ? (s & kBinCount) : 0ull;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+          excl += c;
+          if (first_pre < first_wait) break;
+          if (take == 0) {
             if (++spins > kSpinLimit) {
-              atomicOr(&hdr->status, kStatusTimeout);
+              if (lane == 0) atomicOr(&hdr->status, kStatusTimeout);
               break;
             }
             continue;
           }
-          excl += s & kBinCount;
-          if ((s & (3ull << 30)) == kBinPre) break;
-          --j;
+          j -= take;
         }
-        st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | min(excl + tot, kBinCount));
+        if (lane == 0)
+          st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | min(excl + tot, kBinCount));
       }
-      s_off = excl;
+      if (lane == 0) s_off = excl;
+    }
+    if (tid == 0) {
+      const unsigned long long excl = s_off;
       if (base + kBinTile >= V) {  // last tile: total pair count
         const unsigned long long want = excl + total;
         hdr->pairs_wanted = (uint32_t)min(want, (unsigned long long)0xFFFFFFFFu);

@@ -24,6 +24,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr unsigned long long kFlagAgg = 1ull << 30;
 constexpr unsigned long long kFlagPre = 2ull << 30;
 constexpr unsigned long long kCount30 = (1ull << 30) - 1;
+constexpr int kLookWindow = 8;   // look-back words read per round trip
 
 __device__ __forceinline__ unsigned long long make_status(uint32_t tag, unsigned long long flag,
                                                           uint32_t count) {
@@ -131,21 +132,34 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     st_relaxed64(my, make_status(tag, kFlagPre, tot));
   } else {
     st_relaxed64(my, make_status(tag, kFlagAgg, tot));
+    // kLookWindow predecessors per round trip: their words are loaded together,
+    // then consumed nearest first until a prefix or a word not yet published
     int64_t j = (int64_t)tile - 1;
     uint32_t spins = 0;
-    while (j >= 0) {
-      const unsigned long long s = ld_relaxed64(status + (uint64_t)j * 256 + d);
-      const bool ready = (uint32_t)(s >> 32) == tag && (s & (3ull << 30)) != 0;
-      if (!ready) {
+    bool found = false;
+    while (j >= 0 && !found) {
+      unsigned long long w[kLookWindow];
+#pragma unroll
+      for (int i = 0; i < kLookWindow; ++i)
+        w[i] = j - i >= 0 ? ld_relaxed64(status + (uint64_t)(j - i) * 256 + d) : 0ull;
+      int used = 0;
+#pragma unroll
+      for (int i = 0; i < kLookWindow; ++i) {
+        if (found || used < i || j - i < 0) break;
+        const bool ready = (uint32_t)(w[i] >> 32) == tag && (w[i] & (3ull << 30)) != 0;
+        if (!ready) break;
+        excl += (uint32_t)(w[i] & kCount30);
+        used = i + 1;
+        found = (w[i] & (3ull << 30)) == kFlagPre;
+      }
+      if (used == 0) {
         if (++spins > kSpinLimit) {
           atomicOr(status_word, kStatusTimeout);
           break;
         }
         continue;
       }
-      excl += (uint32_t)(s & kCount30);
-      if ((s & (3ull << 30)) == kFlagPre) break;
-      --j;
+      j -= used;
     }
     st_relaxed64(my, make_status(tag, kFlagPre, (uint32_t)min((unsigned long long)excl + tot, kCount30)));
   }

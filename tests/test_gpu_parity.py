@@ -292,7 +292,7 @@ def test_backward_dense_with_t_culling():
     _check_backward(scene_np, cam, gs.RasterOpts(sh_degree=1, t_cull=1e-2), g)
 
 
-@pytest.mark.parametrize("mode,thr", [("naive", 0), ("warp", 8), ("warp", 33)])
+@pytest.mark.parametrize("mode,thr", [("naive", 0), ("warp", 8), ("warp", 33), ("warp", 1)])
 def test_reduction_modes_agree(mode, thr):
     """The reduction is exactly a sum: every mode gives the same per-splat
     accumulators up to FP32 reassociation."""
