@@ -108,18 +108,151 @@ __device__ __forceinline__ bool project_core(const CamDev& cam, float mx, float 
   return true;
 }
 
+// One splat's SH coefficients, 3 (DEG + 1)^2 floats.  When a row is a whole
+// number of 16-byte words (SH degree 1 or 3) and the array is 16-byte aligned,
+// it is read as float4s: a quarter of the memory instructions.
+template <int DEG>
+struct ShRow {
+  static constexpr int kN = 3 * (DEG + 1) * (DEG + 1);
+  static constexpr bool kVec = kN % 4 == 0;
+  float v[kN];
+  __device__ __forceinline__ void load(const float* __restrict__ p, bool vec) {
+    if (kVec && vec) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+      for (int i = 0; i < kN / 4; ++i) {
+        const float4 t = q[i];
+        v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kN; ++i) v[i] = p[i];
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
-// Forward projection.  Persistent grid-stride loop so that each CTA flushes
-// its shared-memory digit histograms to global memory once.
+// Forward projection.
+//
+// Only a fraction of the splats is visible, scattered over the index range,
+// so a warp that ran the full projection on 32 consecutive splats would
+// execute it whenever one lane needed it.  Each warp therefore first runs a
+// cheap, conservative test on 32 consecutive splats (mean, opacity, scale:
+// near plane, opacity floor, and a screen test with an upper bound of the
+// ellipse's extent) and queues the survivors in shared memory; every time 32
+// are queued it projects them with all lanes busy.  The depth keys stay
+// indexed by splat id, so the sort sees them in index order.
+// Persistent grid-stride loop so that each CTA flushes its shared-memory digit
+// histograms to global memory once.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) project_fwd_kernel(
+constexpr int kProjThreads = 256;
+constexpr int kProjWarps = kProjThreads / 32;
+
+// Cheap test: false only for splats the full projection would cull.
+__device__ __forceinline__ bool may_be_visible(const CamDev& cam, float mx, float my, float mz,
+                                               float o, float sx, float sy, float sz) {
+  if (!(o * 255.0f >= 1.0f)) return false;
+  const float tz = ff_dot3_add(&cam.R[6], mx, my, mz, cam.t[2]).hi;   // as in project_core
+  if (!(tz > cam.znear)) return false;
+  const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
+  const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
+  const float iz = 1.f / tz;
+  const float ax = tx * iz, ay = ty * iz;
+  // |J|_2^2 <= |J|_F^2 and |W R S|_2 = max scale bound the largest eigenvalue of Sigma_2D
+  const float F2 = (cam.fx * cam.fx * fmaf(ax, ax, 1.f) + cam.fy * cam.fy * fmaf(ay, ay, 1.f)) * iz * iz;
+  const float smax = fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz)));
+  const float k = fmaxf(0.f, 2.0f * kLn2 * log2f(255.0f * o));
+  const float r = sqrtf(k * fmaf(F2, smax * smax, kDilation)) * 1.01f + 1.0f;
+  const float ux = fmaf(cam.fx, ax, cam.cx), uy = fmaf(cam.fy, ay, cam.cy);
+  const float mx_ = 1.0f + 1e-4f * fabsf(ux), my_ = 1.0f + 1e-4f * fabsf(uy);
+  return ux + r >= 0.5f - mx_ && ux - r <= (float)cam.W - 0.5f + mx_ &&
+         uy + r >= 0.5f - my_ && uy - r <= (float)cam.H - 0.5f + my_;
+}
+
+// The full projection of splat i: returns its depth key (kNone when culled)
+// and writes its record and block box.  DEG is the SH degree (0..3).
+template <int DEG>
+__device__ __forceinline__ uint32_t project_splat(
+    int i, const float* __restrict__ means, const float* __restrict__ scales,
+    const float4* __restrict__ quats, const float* __restrict__ opac, const float* __restrict__ sh,
+    bool sh_vec, const CamDev& cam, int clamp01, SplatRec* __restrict__ rec,
+    uint2* __restrict__ boxes) {
+  const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+  const float o = opac[i];
+  ProjState ps;
+  bool ok = o * 255.0f >= 1.0f;   // opacity floor: alpha <= o < 1/255 everywhere
+  if (ok) ok = project_core(cam, mx, my, mz, quats[i], scales[3 * i], scales[3 * i + 1],
+                            scales[3 * i + 2], ps);
+  if (ok) ok = ps.det > 0.f;
+  if (!ok) return kNone;
+  // screen centre in float-float: t = W mu + w and mu_2D = f t_xy / t_z + c
+  const FF tx = ff_dot3_add(&cam.R[0], mx, my, mz, cam.t[0]);
+  const FF ty = ff_dot3_add(&cam.R[3], mx, my, mz, cam.t[1]);
+  const FF tz = ff_dot3_add(&cam.R[6], mx, my, mz, cam.t[2]);
+  const FF fux = ff_add_f(ff_mul_f(ff_div(tx, tz), cam.fx), cam.cx);
+  const FF fuy = ff_add_f(ff_mul_f(ff_div(ty, tz), cam.fy), cam.cy);
+  const float ux = fux.hi, uy = fuy.hi;
+  // power >= -ln(255 o)  <=>  d^T Q d <= k = 2 ln(255 o); the ellipse's box
+  // has half-widths sqrt(k Sigma_00), sqrt(k Sigma_11).  A small relative
+  // and absolute widening keeps every fragment the FP32 raster accepts.
+  const float thr = -log2f(255.0f * o);
+  const float k = fmaxf(0.f, -2.0f * kLn2 * thr);
+  const float ex = sqrtf(k * ps.s00) * 1.002f + 0.02f;
+  const float ey = sqrtf(k * ps.s11) * 1.002f + 0.02f;
+  // any pixel centre (x + 0.5, y + 0.5) inside the box?
+  const float x0 = ceilf(ux - ex - 0.5f), x1 = floorf(ux + ex - 0.5f);
+  const float y0 = ceilf(uy - ey - 0.5f), y1 = floorf(uy + ey - 0.5f);
+  if (!(x0 <= x1 && y0 <= y1 && x1 >= 0.f && y1 >= 0.f && x0 <= (float)(cam.W - 1) &&
+        y0 <= (float)(cam.H - 1)))
+    return kNone;
+  // 16x16 blocks of the pixel-centre box (clamped to the image)
+  const int bx0 = (int)fmaxf(x0, 0.f) >> 4, bx1 = (int)fminf(x1, (float)(cam.W - 1)) >> 4;
+  const int by0 = (int)fmaxf(y0, 0.f) >> 4, by1 = (int)fminf(y1, (float)(cam.H - 1)) >> 4;
+  boxes[i] = make_uint2((uint32_t)bx0 | ((uint32_t)by0 << 16),
+                        (uint32_t)(bx1 - bx0 + 1) | ((uint32_t)(by1 - by0 + 1) << 16));
+  // colour from SH at the view direction
+  float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+  const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+  vx *= rn; vy *= rn; vz *= rn;
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  float Y[16];
+  sh_eval(DEG, vx, vy, vz, Y);
+  ShRow<DEG> row;
+  row.load(sh + (size_t)i * K * 3, sh_vec);
+  float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int kk = 0; kk < K; ++kk) {
+    col[0] += row.v[kk * 3 + 0] * Y[kk];
+    col[1] += row.v[kk * 3 + 1] * Y[kk];
+    col[2] += row.v[kk * 3 + 2] * Y[kk];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    col[c] = fmaxf(0.f, col[c]);
+    if (clamp01) col[c] = fminf(1.f, col[c]);
+  }
+  // inverse Cholesky factor of Sigma_2D, scaled so that
+  // q = (i11 dx)^2 + (i22 (dy - k dx))^2 = -log2(e) * power
+  const float sc = 0.84932180028801904f;   // sqrt(log2(e) / 2)
+  SplatRec r;
+  r.a = make_float4(ux, uy, sc * rsqrtf(ps.s00), ps.s01 / ps.s00);
+  r.b = make_float4(sc * sqrtf(ps.s00 / ps.det), -thr, fux.lo, fuy.lo);
+  r.c = make_float4(col[0], col[1], col[2], o);
+  rec[i] = r;
+  return __float_as_uint(ps.t[2]);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads, 3) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float4* __restrict__ quats, const float* __restrict__ opac,
-    const float* __restrict__ sh, int n, int deg, CamDev cam, int clamp01,
+    const float* __restrict__ sh, int n, CamDev cam, int clamp01, int sh_vec,
     SplatRec* __restrict__ rec, uint2* __restrict__ boxes, uint32_t* __restrict__ keys,
     Header* __restrict__ hdr, uint2* __restrict__ ranges, int n_ranges,
     uint32_t* __restrict__ epoch) {
   __shared__ uint32_t s_hist[4][256];
+  __shared__ int s_queue[kProjWarps][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // a new view: look-back status words of earlier views stop matching
   if (blockIdx.x == 0 && threadIdx.x == 0) *epoch += 1u;
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
@@ -127,70 +260,16 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ranges; i += gridDim.x * blockDim.x)
     ranges[i] = make_uint2(0, 0);
   __syncthreads();
-  const int K = (deg + 1) * (deg + 1);
+  int* q = s_queue[warp];
+  int queued = 0;                       // warp-uniform
   uint32_t local_visible = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t key = kNone;
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-    const float o = opac[i];
-    ProjState ps;
-    bool ok = o * 255.0f >= 1.0f;   // opacity floor: alpha <= o < 1/255 everywhere
-    if (ok) ok = project_core(cam, mx, my, mz, quats[i], scales[3 * i], scales[3 * i + 1],
-                              scales[3 * i + 2], ps);
-    if (ok) ok = ps.det > 0.f;
-    if (ok) {
-      // screen centre in float-float: t = W mu + w and mu_2D = f t_xy / t_z + c
-      const FF tx = ff_dot3_add(&cam.R[0], mx, my, mz, cam.t[0]);
-      const FF ty = ff_dot3_add(&cam.R[3], mx, my, mz, cam.t[1]);
-      const FF tz = ff_dot3_add(&cam.R[6], mx, my, mz, cam.t[2]);
-      const FF fux = ff_add_f(ff_mul_f(ff_div(tx, tz), cam.fx), cam.cx);
-      const FF fuy = ff_add_f(ff_mul_f(ff_div(ty, tz), cam.fy), cam.cy);
-      const float ux = fux.hi, uy = fuy.hi;
-      // power >= -ln(255 o)  <=>  d^T Q d <= k = 2 ln(255 o); the ellipse's box
-      // has half-widths sqrt(k Sigma_00), sqrt(k Sigma_11).  A small relative
-      // and absolute widening keeps every fragment the FP32 raster accepts.
-      const float thr = -log2f(255.0f * o);
-      const float k = fmaxf(0.f, -2.0f * kLn2 * thr);
-      const float ex = sqrtf(k * ps.s00) * 1.002f + 0.02f;
-      const float ey = sqrtf(k * ps.s11) * 1.002f + 0.02f;
-      // any pixel centre (x + 0.5, y + 0.5) inside the box?
-      const float x0 = ceilf(ux - ex - 0.5f), x1 = floorf(ux + ex - 0.5f);
-      const float y0 = ceilf(uy - ey - 0.5f), y1 = floorf(uy + ey - 0.5f);
-      ok = x0 <= x1 && y0 <= y1 && x1 >= 0.f && y1 >= 0.f && x0 <= (float)(cam.W - 1) &&
-           y0 <= (float)(cam.H - 1);
-      if (ok) {
-        // 16x16 blocks of the pixel-centre box (clamped to the image)
-        const int bx0 = (int)fmaxf(x0, 0.f) >> 4, bx1 = (int)fminf(x1, (float)(cam.W - 1)) >> 4;
-        const int by0 = (int)fmaxf(y0, 0.f) >> 4, by1 = (int)fminf(y1, (float)(cam.H - 1)) >> 4;
-        boxes[i] = make_uint2((uint32_t)bx0 | ((uint32_t)by0 << 16),
-                              (uint32_t)(bx1 - bx0 + 1) | ((uint32_t)(by1 - by0 + 1) << 16));
-        // colour from SH at the view direction
-        float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
-        const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
-        vx *= rn; vy *= rn; vz *= rn;
-        float Y[16];
-        sh_eval(deg, vx, vy, vz, Y);
-        const float* shp = sh + (size_t)i * K * 3;
-        float col[3] = {0.5f, 0.5f, 0.5f};
-        for (int kk = 0; kk < K; ++kk) {
-          col[0] += shp[kk * 3 + 0] * Y[kk];
-          col[1] += shp[kk * 3 + 1] * Y[kk];
-          col[2] += shp[kk * 3 + 2] * Y[kk];
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          col[c] = fmaxf(0.f, col[c]);
-          if (clamp01) col[c] = fminf(1.f, col[c]);
-        }
-        // inverse Cholesky factor of Sigma_2D, scaled so that
-        // q = (i11 dx)^2 + (i22 (dy - k dx))^2 = -log2(e) * power
-        const float sc = 0.84932180028801904f;   // sqrt(log2(e) / 2)
-        SplatRec r;
-        r.a = make_float4(ux, uy, sc * rsqrtf(ps.s00), ps.s01 / ps.s00);
-        r.b = make_float4(sc * sqrtf(ps.s00 / ps.det), -thr, fux.lo, fuy.lo);
-        r.c = make_float4(col[0], col[1], col[2], o);
-        rec[i] = r;
-        key = __float_as_uint(ps.t[2]);
+  auto project_queued = [&](int count) {
+    if (lane < count) {
+      const int i = q[lane];
+      const uint32_t key = project_splat<DEG>(i, means, scales, quats, opac, sh, sh_vec != 0, cam,
+                                              clamp01, rec, boxes);
+      keys[i] = key;
+      if (key != kNone) {
         local_visible++;
         atomicAdd(&s_hist[0][key & 0xFF], 1u);
         atomicAdd(&s_hist[1][(key >> 8) & 0xFF], 1u);
@@ -198,12 +277,33 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         atomicAdd(&s_hist[3][key >> 24], 1u);
       }
     }
-    keys[i] = key;
+  };
+  const int64_t warps_total = (int64_t)gridDim.x * kProjWarps;
+  for (int64_t base = ((int64_t)blockIdx.x * kProjWarps + warp) * 32; base < n;
+       base += warps_total * 32) {
+    const int i = (int)base + lane;
+    bool cand = false;
+    if (i < n)
+      cand = may_be_visible(cam, means[3 * i], means[3 * i + 1], means[3 * i + 2], opac[i],
+                            scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]);
+    if (i < n && !cand) keys[i] = kNone;
+    const uint32_t m = __ballot_sync(0xffffffffu, cand);
+    if (cand) q[queued + __popc(m & lanemask_lt())] = i;
+    queued += __popc(m);
+    __syncwarp();
+    if (queued >= 32) {
+      project_queued(32);
+      __syncwarp();
+      queued -= 32;
+      if (lane < queued) q[lane] = q[32 + lane];
+      __syncwarp();
+    }
   }
+  project_queued(queued);
   // visible count: warp-aggregate, one atomic per warp
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) local_visible += __shfl_xor_sync(0xffffffffu, local_visible, off);
-  if ((threadIdx.x & 31) == 0 && local_visible) atomicAdd(&hdr->visible, local_visible);
+  if (lane == 0 && local_visible) atomicAdd(&hdr->visible, local_visible);
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
     const uint32_t v = (&s_hist[0][0])[i];
@@ -389,13 +489,24 @@ cudaError_t launch_project_fwd(const float* means, const float* scales, const fl
                                const gs_camera& cam, int clamp01, SplatRec* rec, uint2* boxes,
                                uint32_t* keys, Header* hdr, uint2* ranges, int n_ranges,
                                uint32_t* epoch, int num_sms, cudaStream_t st) {
-  int blocks = (n + 255) / 256;
+  int blocks = (n + kProjThreads - 1) / kProjThreads;
   const int cap = num_sms * 8;  // persistent: a few waves' worth of CTAs
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  project_fwd_kernel<<<blocks, 256, 0, st>>>(means, scales, reinterpret_cast<const float4*>(quats),
-                                             opac, sh, n, deg, make_cam(cam), clamp01, rec, boxes,
-                                             keys, hdr, ranges, n_ranges, epoch);
+  const float4* q4 = reinterpret_cast<const float4*>(quats);
+  const CamDev cd = make_cam(cam);
+  const int sh_vec = ((uintptr_t)sh & 15) == 0;
+#define GS_PROJECT_FWD(D)                                                                        \
+  project_fwd_kernel<D><<<blocks, kProjThreads, 0, st>>>(means, scales, q4, opac, sh, n, cd,     \
+                                                         clamp01, sh_vec, rec, boxes, keys, hdr, \
+                                                         ranges, n_ranges, epoch)
+  switch (deg) {
+    case 0: GS_PROJECT_FWD(0); break;
+    case 1: GS_PROJECT_FWD(1); break;
+    case 2: GS_PROJECT_FWD(2); break;
+    default: GS_PROJECT_FWD(3); break;
+  }
+#undef GS_PROJECT_FWD
   return cudaGetLastError();
 }
 
