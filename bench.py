@@ -223,8 +223,7 @@ def run_ours(args, rank, world, local_rank):
     n_front = int(((scene.means @ torch.as_tensor(cam.viewmat[2, :3], device=dev)) +
                    float(cam.viewmat[2, 3]) > 0.2).sum().item())
     V, P = cnt["visible"], cnt["pairs"]
-    rg = gs.copy_array(ws, _lib.GS_ARRAY_RANGES, cnt["blocks"], stream).to(torch.int64)
-    P_live = int((rg[:, 1] - rg[:, 0]).sum().item())
+    P_live = cnt["live_pairs"]
     npix = H * W
     passes = ws.c.pair_passes
     # bin: count, emit, pair-sort passes, ranges, item order; blend_bwd: item reorder + raster
@@ -235,7 +234,9 @@ def run_ours(args, rank, world, local_rank):
     alg = {
         "project": ("hbm", scene.n * 20 + n_front * 28 + V * (12 * K_sh + 48)),
         "sort": ("hbm", scene.n * 4 + 56 * V),
-        "bin": ("hbm", 148 * V + (8 + 16 * passes + 4) * P),
+        # emission writes P pairs, the first pass reads them and writes the live
+        # ones, later passes move live pairs, the ranges kernel reads them
+        "bin": ("hbm", 148 * V + 16 * P + (8 + 16 * (passes - 1) + 4) * P_live),
         "blend_fwd": ("alu", FLOP_PER_FRAG_FWD * F),
         "loss": ("hbm", 36 * npix),
         "blend_bwd": ("alu", FLOP_PER_FRAG_BWD * F),

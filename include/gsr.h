@@ -244,9 +244,11 @@ int gs_check_status(gs_workspace* ws, gs_stream_t stream);
 const char* gs_last_error(void);
 
 /* Introspection for tests and metrics.  gs_read_counters synchronises `stream`
- * and writes (host) out[0] = visible splats V, out[1] = pairs P, out[2] =
- * device status, out[3] = 16x16 blocks of the bound camera, out[4] = pairs the
- * view needs (above out[1] when the pair capacity was exceeded).  out holds 5. */
+ * and writes (host) out[0] = visible splats V, out[1] = (splat, block) pairs P
+ * of the splats' block boxes, out[2] = device status, out[3] = 16x16 blocks of
+ * the bound camera, out[4] = pairs the view needs (above out[1] when the pair
+ * capacity was exceeded), out[5] = live pairs (those whose block the splat's
+ * ellipse reaches: the sorted pair arrays hold these).  out holds 6. */
 int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
 
 /* Copies an internal array of `ws` into caller device memory `dst` (`bytes`):
@@ -255,8 +257,8 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
  * r, g, b, o: the screen centre mu + mu_lo as a float-float pair, the inverse
  * Cholesky factor of Sigma_2D scaled so that (i11 dx)^2 + (i22 (dy - k dx))^2 =
  * -log2(e) * power, and tau = log2(255 o)),
- * GS_ARRAY_PAIR_BLOCKS u32 [P], GS_ARRAY_PAIR_RANKS u32 [P] (sorted by block; a
- * block id equal to the block count marks a box block the ellipse misses),
+ * GS_ARRAY_PAIR_BLOCKS u32 [live pairs], GS_ARRAY_PAIR_RANKS u32 [live pairs]
+ * (sorted by block, depth order within a block),
  * GS_ARRAY_RANGES u32 [blocks][2], GS_ARRAY_GRAD2D float [V][12] (per depth
  * rank: the backward's unscaled accumulators), GS_ARRAY_BOXES u32 [V][2] (per
  * depth rank: first block x | y << 16, box width | height << 16 in blocks). */

@@ -330,10 +330,10 @@ def check_status(ws: Workspace, stream=None):
 
 
 def read_counters(ws: Workspace, stream=None) -> dict:
-    out = (ctypes.c_int64 * 5)()
+    out = (ctypes.c_int64 * 6)()
     check(_lib.load().gs_read_counters(ws.ref, out, _stream(stream)), "gs_read_counters")
     return dict(visible=int(out[0]), pairs=int(out[1]), status=int(out[2]), blocks=int(out[3]),
-                pairs_wanted=int(out[4]))
+                pairs_wanted=int(out[4]), live_pairs=int(out[5]))
 
 
 _ARRAY_DTYPES = {

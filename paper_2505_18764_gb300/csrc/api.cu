@@ -269,7 +269,7 @@ int gs_project(gs_workspace* ws, const float* means, const float* scales, const 
   ws->sh_degree = opts->sh_degree;
   ws->state_format = opts->state_format;
   ws->clamp01 = opts->state_format == GS_STATE_UNORM16 || opts->state_format == GS_STATE_UNORM8;
-  ws->pair_passes = pair_passes_for(blocks + 1);   // ids 0..blocks (blocks = missed)
+  ws->pair_passes = pair_passes_for(blocks);   // block ids 0..blocks-1
   GS_CUDA(cudaMemsetAsync(at<Header>(ws, L_HDR), 0, sizeof(Header), st), "gs_project memset");
   GS_CUDA(launch_project_fwd(means, scales, quats, opacities, sh, n, opts->sh_degree, *cam,
                              ws->clamp01, at<SplatRec>(ws, L_REC), at<uint2>(ws, L_BOXES_ID),
@@ -336,10 +336,13 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
   uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};
   for (int q = 0; q < ws->pair_passes; ++q) {
+    // the first pass reads every emitted pair and drops the missed ones (key
+    // 0xFFFFFFFF); the others see only the live pairs
     GS_CUDA(launch_onesweep_pass(pk[q & 1], pv[q & 1], pk[(q + 1) & 1], pv[(q + 1) & 1],
-                                 &hdr->pairs, 0u, (uint32_t)ws->pair_cap, (uint32_t)ws->pair_cap,
-                                 8 * q, 0xFFu, hdr->pair_hist[q], at<unsigned long long>(ws, L_STATUS),
-                                 &hdr->tile_counter[4 + q], epoch, 4u + q, &hdr->status, 0,
+                                 q == 0 ? &hdr->pairs : &hdr->live_pairs, 0u,
+                                 (uint32_t)ws->pair_cap, (uint32_t)ws->pair_cap, 8 * q, 0xFFu,
+                                 hdr->pair_hist[q], at<unsigned long long>(ws, L_STATUS),
+                                 &hdr->tile_counter[4 + q], epoch, 4u + q, &hdr->status, q == 0,
                                  grid_cap, st),
             "pair sort pass");
   }
@@ -513,8 +516,8 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream) {
   if (rc) return rc;
   if (!out) return fail(GS_ERR_INVALID_ARG, "out is null");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  uint32_t h[4] = {0, 0, 0, 0};   // status, visible, pairs, pairs_wanted
-  GS_CUDA(cudaMemcpyAsync(h, at<Header>(ws, L_HDR), 16, cudaMemcpyDeviceToHost, st), "counter copy");
+  uint32_t h[5] = {0, 0, 0, 0, 0};   // status, visible, pairs, pairs_wanted, live_pairs
+  GS_CUDA(cudaMemcpyAsync(h, at<Header>(ws, L_HDR), 20, cudaMemcpyDeviceToHost, st), "counter copy");
   GS_CUDA(cudaStreamSynchronize(st), "counter sync");
   int gw, gh;
   out[0] = h[1];
@@ -522,6 +525,7 @@ int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream) {
   out[2] = h[0];
   out[3] = blocks_of(ws->width, ws->height, gw, gh);
   out[4] = h[3];
+  out[5] = h[4];
   return GS_OK;
 }
 

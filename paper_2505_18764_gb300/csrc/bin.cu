@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
   for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
   const uint32_t P = hdr->pairs, V = hdr->visible;
   const uint32_t nchunks = (P + kEmitChunk - 1) / kEmitChunk;
+  uint32_t live = 0;
   for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const uint32_t p0 = c * kEmitChunk;
     const uint32_t p1 = min(P, p0 + kEmitChunk);
@@ -203,16 +204,22 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
       const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
       const uint32_t bx = (box.x & 0xFFFFu) + k % w;
       const uint32_t by = (box.x >> 16) + min(k / w, h - 1);  // stays inside the box
-      // blocks of the box that the ellipse misses get the sentinel id gw * gh:
-      // they sort behind every real block and no block's range includes them
+      // blocks of the box that the ellipse misses get the key 0xFFFFFFFF, which
+      // the first pass of the pair sort drops
       const SplatRec& R = rec_sorted[r0 + lo];
       const bool hit = block_may_hit(R.a, R.b, (float)(bx * kBlock) + 0.5f, (float)(by * kBlock) + 0.5f);
-      const uint32_t key = hit ? by * (uint32_t)gw + bx : (uint32_t)(gw * gh);
+      const uint32_t key = hit ? by * (uint32_t)gw + bx : kNone;
       pair_keys[p] = key;
       pair_vals[p] = r0 + lo;
-      for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
+      if (hit) {
+        ++live;
+        for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
+      }
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(0xffffffffu, live, o);
+  if ((tid & 31) == 0 && live) atomicAdd(&hdr->live_pairs, live);
   __syncthreads();
   for (int i = tid; i < pair_passes * 256; i += kBinThreads) {
     const uint32_t v = (&s_hist[0][0])[i];
@@ -220,15 +227,15 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
   }
 }
 
-// Block ranges [start, end) in the pairs sorted by block id.  ranges must be
-// zero beforehand (the projection kernel clears them).
+// Block ranges [start, end) in the live pairs sorted by block id.  ranges must
+// be zero beforehand (the projection kernel clears them).
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys,
                                                      const Header* __restrict__ hdr,
                                                      uint2* __restrict__ ranges, uint32_t nblocks) {
-  const uint32_t P = hdr->pairs;
+  const uint32_t P = hdr->live_pairs;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
     const uint32_t k = keys[i];
-    if (k >= nblocks) continue;   // pairs whose block the ellipse misses
+    if (k >= nblocks) continue;
     if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
     if (i + 1 == P || keys[i + 1] != k) ranges[k].y = i + 1;
   }

@@ -105,31 +105,32 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     opts = gs.RasterOpts()
     scene, ws, _ = run_forward(scene_np, cam, opts)
     cnt = gs.read_counters(ws)
-    V, P = cnt["visible"], cnt["pairs"]
-    blocks = gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_BLOCKS, P).cpu().numpy().astype(np.int64)
-    ranks = gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_RANKS, P).cpu().numpy().astype(np.int64)
+    V, P, PL = cnt["visible"], cnt["pairs"], cnt["live_pairs"]
+    assert 0 < PL <= P
+    blocks = gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_BLOCKS, PL).cpu().numpy().astype(np.int64)
+    ranks = gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_RANKS, PL).cpu().numpy().astype(np.int64)
     ranges = gs.copy_array(ws, gs._lib.GS_ARRAY_RANGES, cnt["blocks"]).cpu().numpy().astype(np.int64)
-    assert np.all(np.diff(blocks) >= 0)
     nblk = cnt["blocks"]
-    live = blocks < nblk
-    same = (np.diff(blocks) == 0) & live[1:]
+    assert np.all(blocks < nblk) and np.all(np.diff(blocks) >= 0)
+    same = np.diff(blocks) == 0
     assert np.all(np.diff(ranks)[same] > 0), "depth order lost inside a block"
-    assert np.all(np.diff(ranks)[~live[1:] & ~live[:-1]] >= 0)   # missed blocks keep rank order
-    assert np.all(blocks[~live] == nblk) and live.sum() > 0
-    # ranges delimit each block's run
-    for b in np.unique(blocks[live]):
+    # ranges delimit each block's run, and the runs cover the pairs
+    assert (ranges[:, 1] - ranges[:, 0]).sum() == PL
+    for b in np.unique(blocks):
         s, e = ranges[b]
-        assert np.all(blocks[s:e] == b) and (s == 0 or blocks[s - 1] != b) and (e == P or blocks[e] != b)
-    # each splat's pairs are exactly the blocks of its box, and every box holds
-    # the blocks the oracle's alpha >= 1/255 ellipse reaches
+        assert np.all(blocks[s:e] == b) and (s == 0 or blocks[s - 1] != b) and (e == PL or blocks[e] != b)
+    # each splat's pairs lie in the blocks of its box, at most one per block
     boxes = gs.copy_array(ws, gs._lib.GS_ARRAY_BOXES, V).cpu().numpy().astype(np.int64)
     bx0, by0 = boxes[:, 0] & 0xFFFF, boxes[:, 0] >> 16
     w, h = boxes[:, 1] & 0xFFFF, boxes[:, 1] >> 16
-    np.testing.assert_array_equal(np.bincount(ranks, minlength=V), w * h)
+    assert np.all(np.bincount(ranks, minlength=V) <= w * h)
+    assert P == int((w * h).sum())
     gw = (cam.width + 15) // 16
-    pbx, pby = blocks[live] % gw, blocks[live] // gw
-    rl = ranks[live]
-    assert np.all((pbx >= bx0[rl]) & (pbx < bx0[rl] + w[rl]) & (pby >= by0[rl]) & (pby < by0[rl] + h[rl]))
+    pbx, pby = blocks % gw, blocks // gw
+    assert np.all((pbx >= bx0[ranks]) & (pbx < bx0[ranks] + w[ranks]) & (pby >= by0[ranks]) &
+                  (pby < by0[ranks] + h[ranks]))
+    assert len(np.unique(ranks * nblk + blocks)) == PL
+    # every box holds the blocks the oracle's alpha >= 1/255 ellipse reaches
     ids = gs.copy_array(ws, gs._lib.GS_ARRAY_SORTED_IDS, V).cpu().numpy()
     Pj = oracle.project(scene_np, cam)[ids]
     o = scene_np.opacities[ids].astype(np.float64)
@@ -140,6 +141,20 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     y0 = np.clip(np.ceil(Pj[:, 2] - ey - 0.5), 0, cam.height - 1).astype(np.int64) >> 4
     y1 = np.clip(np.floor(Pj[:, 2] + ey - 0.5), 0, cam.height - 1).astype(np.int64) >> 4
     assert np.all((bx0 <= x0) & (bx0 + w - 1 >= x1) & (by0 <= y0) & (by0 + h - 1 >= y1))
+    # and a live pair for every block holding a pixel centre with alpha >= 1/255
+    # (outside a 1e-6 band of the cut), by brute force over each box
+    live = set((ranks * nblk + blocks).tolist())
+    for r in range(V):
+        xs = np.arange(max(0, int(np.floor(Pj[r, 1] - ex[r])) - 1), min(cam.width, int(np.ceil(Pj[r, 1] + ex[r])) + 2))
+        ys = np.arange(max(0, int(np.floor(Pj[r, 2] - ey[r])) - 1), min(cam.height, int(np.ceil(Pj[r, 2] + ey[r])) + 2))
+        X, Y = np.meshgrid(xs + 0.5, ys + 0.5)
+        dx, dy = X - Pj[r, 1], Y - Pj[r, 2]
+        power = -0.5 * (Pj[r, 6] * dx * dx + 2 * Pj[r, 7] * dx * dy + Pj[r, 8] * dy * dy)
+        cut = np.log(1.0 / (255.0 * o[r]))
+        inside = power >= cut + 1e-6 * max(1.0, abs(cut))
+        for yy, xx in zip(*np.nonzero(inside)):
+            b = (int(ys[yy]) >> 4) * gw + (int(xs[xx]) >> 4)
+            assert r * nblk + b in live, (r, b)
 
 
 # ---------------------------------------------------------------------------
