@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=48, help="pixels in the CPU-baseline sample")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--ablation-only", action="store_true",
+                    help="only the gradient-reduction ablation (one backward raster per mode after "
+                         "a warm-up; for counting atomics under a profiler)")
     return ap.parse_args()
 
 
@@ -208,6 +212,9 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step32()
     torch.cuda.synchronize(dev)
+    if args.ablation_only:
+        return dict(metric=METRIC, reduction_ablation=run_ablation(gs, torch, ws, ccam, state32, last,
+                                                                   dl, stream, None, reps=1))
     if not args.no_extras:
         clocks.start()
     total_ms, per_stage, step_ms, t_wall = timed(step32, args.steps, 0)
@@ -301,12 +308,85 @@ def run_ours(args, rank, world, local_rank):
         del ws16
         res["e2e"] = run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, state32,
                              last, dl, loss, grads, ws)
+        res["reduction_ablation"] = run_ablation(gs, torch, ws, ccam, state32, last, dl, stream, F)
+        if not args.no_training:
+            res["training"] = run_training(args, dev)
         res["clocks"] = clk
         if not args.no_serving:
             res["serving"] = run_serving(args, dev)
         if world == 1:
             res["cpu_baseline"] = cpu_baseline(args, scene_np, cam, target_np)
     return res
+
+
+# Gradient reduction modes of the backward raster (the paper's Sec. 3.2 ablation):
+# per-fragment atomics, and the warp reduction with balancing thresholds X.
+ABLATION = (("naive", 0), ("warp", 1), ("warp", 4), ("warp", 8), ("warp", 16), ("warp", 33))
+
+
+def run_ablation(gs, torch, ws, ccam, state, last, dl, stream, F, reps=10):
+    """Backward-raster time per reduction mode on the view the workspace holds
+    (binning, state and dL/dC from the last step)."""
+    out = []
+    for mode, x in ABLATION:
+        o = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4, reduce_mode=mode,
+                          reduce_threshold=x)
+        gs.blend_backward(ws, ccam, o, state, last, dl, stream)   # warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for k in range(reps):
+            ev[2 * k].record(stream)
+            gs.blend_backward(ws, ccam, o, state, last, dl, stream)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.median([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)]))
+        row = dict(mode=mode, X=x, blend_bwd_ms=round(ms, 4))
+        if F:
+            row["splat_frags_per_s"] = round(F / (ms * 1e-3), 1)
+        out.append(row)
+    return out
+
+
+def run_training(args, dev):
+    """Training step through torch.autograd: 1.0M splats (tiny-scene
+    distributions, SH3), 8 orbit views at 1600x1060, FP16 state, summed L2
+    loss per view, then an Adam step (lr 1e-3) on every parameter."""
+    import torch
+    import synthetic as syn
+    from paper_2505_18764_gb300 import RasterOpts
+    from paper_2505_18764_gb300.autograd import Renderer
+    scene_np, cams, targets = syn.training_scene_1m()
+    model = Renderer(scene_np, 1600, 1060, RasterOpts(state_format="fp16", sh_degree=3),
+                     device=dev)
+    tg = [torch.from_numpy(t).to(dev) for t in targets]
+    optim = torch.optim.Adam(model.parameters(), lr=1e-3)
+
+    def step():
+        optim.zero_grad(set_to_none=False)
+        total = torch.zeros((), dtype=torch.float32, device=dev)
+        for cam, t in zip(cams, tg):
+            loss = ((model(cam) - t) ** 2).sum()
+            loss.backward()
+            total += loss.detach()
+        optim.step()
+        return total
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    K = 5
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record()
+    losses = []
+    for k in range(K):
+        losses.append(step())
+        ev[k + 1].record()
+    torch.cuda.synchronize(dev)
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    return dict(config="1.0M splats SH3, 8 views 1600x1060, fp16 state, summed L2, Adam lr 1e-3",
+                ms_per_step=round(float(np.median(ms)), 3),
+                ms_per_view=round(float(np.median(ms)) / len(cams), 3),
+                loss_first=round(float(losses[0].item()), 1), loss_last=round(float(losses[-1].item()), 1),
+                steps=K)
 
 
 def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, state, last, dl, loss,
