@@ -309,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
         res["e2e"] = run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, state32,
                              last, dl, loss, grads, ws)
         res["reduction_ablation"] = run_ablation(gs, torch, ws, ccam, state32, last, dl, stream, F)
+        res["back_to_front"] = run_backward_order(gs, torch, ws, ccam, state32, last, dl, stream)
         if not args.no_training:
             res["training"] = run_training(args, dev)
         res["clocks"] = clk
@@ -343,6 +344,24 @@ def run_ablation(gs, torch, ws, ccam, state, last, dl, stream, F, reps=10):
         if F:
             row["splat_frags_per_s"] = round(F / (ms * 1e-3), 1)
         out.append(row)
+    return out
+
+
+def run_backward_order(gs, torch, ws, ccam, state, last, dl, stream, reps=10):
+    """Backward-raster time front to back (the default) and back to front (T
+    recovered by division from the stored final transmittance)."""
+    out = {}
+    for order in ("front_to_back", "back_to_front"):
+        o = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4, backward_order=order)
+        gs.blend_backward(ws, ccam, o, state, last, dl, stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for k in range(reps):
+            ev[2 * k].record(stream)
+            gs.blend_backward(ws, ccam, o, state, last, dl, stream)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        out[order + "_ms"] = round(float(np.median([ev[2 * k].elapsed_time(ev[2 * k + 1])
+                                                    for k in range(reps)])), 4)
     return out
 
 

@@ -68,6 +68,15 @@ enum {
   GS_REDUCE_NAIVE = 1 /* one vector-atomic triple per fragment (the paper's 1x baseline) */
 };
 
+/* Order in which the backward raster visits a pixel's fragments (Sec. 3.1.2).
+ * Front to back (the paper's choice, Eq. 5-7) carries T forward from 1 and C'
+ * from the stored colour.  Back to front starts at the pixel's last fragment
+ * and recovers T_i = T_{i+1} / (1 - alpha_i) from the stored final
+ * transmittance, accumulating the colour behind each fragment (Eq. 4): exact in
+ * FP32 state, but a reduced-precision final T (unorm8 above all) corrupts every
+ * recovered T, which is why the paper traverses front to back. */
+enum { GS_BWD_FRONT_TO_BACK = 0, GS_BWD_BACK_TO_FRONT = 1 };
+
 enum { GS_MODE_FORWARD = 0, GS_MODE_FORWARD_BACKWARD = 1 };
 enum { GS_LOSS_NONE = 0, GS_LOSS_L1 = 1, GS_LOSS_L2 = 2 };
 
@@ -98,6 +107,8 @@ typedef struct gs_raster_opts {
                                two per lane), from 8x this many by sixteen half-warps (4x4);
                                0 = default (GS_SPLIT_THRESHOLD_DEFAULT).  Results do not depend
                                on it. */
+  int32_t backward_order;   /* GS_BWD_* */
+  int32_t reserved;
   int64_t pair_capacity;    /* (splat, 16x16 block) pairs the workspace holds; 0 = 16 per splat */
 } gs_raster_opts;
 

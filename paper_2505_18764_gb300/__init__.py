@@ -18,6 +18,7 @@ from ._lib import (GS_LOSS_L1, GS_LOSS_L2, GS_LOSS_NONE, GS_MODE_FORWARD, GS_MOD
 STATE_FORMATS = {"fp32": 0, "fp16": 1, "unorm16": 2, "unorm8": 3}
 STATE_BYTES = {"fp32": 16, "fp16": 8, "unorm16": 8, "unorm8": 4}
 REDUCE_MODES = {"warp": 0, "naive": 1}
+BACKWARD_ORDERS = {"front_to_back": 0, "back_to_front": 1}
 NONE_RANK = 0xFFFFFFFF
 
 
@@ -31,6 +32,7 @@ class RasterOpts:
     t_cull: float = 1e-4
     pair_capacity: int = 0
     split_threshold: int = 0
+    backward_order: str = "front_to_back"
 
     def to_c(self) -> _lib.GsRasterOpts:
         o = _lib.GsRasterOpts()
@@ -41,6 +43,7 @@ class RasterOpts:
         o.t_cull = float(self.t_cull)
         o.pair_capacity = int(self.pair_capacity)
         o.split_threshold = int(self.split_threshold)
+        o.backward_order = BACKWARD_ORDERS[self.backward_order]
         return o
 
 

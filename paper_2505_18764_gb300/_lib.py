@@ -24,6 +24,7 @@ GS_STATE_FP32, GS_STATE_FP16, GS_STATE_UNORM16, GS_STATE_UNORM8 = 0, 1, 2, 3
 GS_REDUCE_WARP, GS_REDUCE_NAIVE = 0, 1
 GS_SPLIT_THRESHOLD_DEFAULT = 768
 GS_REDUCE_THRESHOLD_DEFAULT = 16
+GS_BWD_FRONT_TO_BACK, GS_BWD_BACK_TO_FRONT = 0, 1
 GS_MODE_FORWARD, GS_MODE_FORWARD_BACKWARD = 0, 1
 GS_LOSS_NONE, GS_LOSS_L1, GS_LOSS_L2 = 0, 1, 2
 GS_SORT_NOALLOC_MAX_PAIRS = 262144
@@ -40,7 +41,8 @@ class GsCamera(Structure):
 class GsRasterOpts(Structure):
     _fields_ = [("state_format", c_int32), ("reduce_mode", c_int32),
                 ("reduce_threshold", c_int32), ("sh_degree", c_int32), ("t_cull", c_float),
-                ("split_threshold", c_int32), ("pair_capacity", c_int64)]
+                ("split_threshold", c_int32), ("backward_order", c_int32), ("reserved", c_int32),
+                ("pair_capacity", c_int64)]
 
 
 class GsWorkspace(Structure):

@@ -35,7 +35,7 @@ cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint
 cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, uint32_t*,
                               const Header*, uint32_t*, const uint32_t*, const SplatRec*, int, int,
                               int, int, float, int, const void*, const uint32_t*, const float*,
-                              float*, int, int, int, cudaStream_t);
+                              float*, int, int, int, int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
                         cudaStream_t);
 size_t sort_tiles(size_t n);
@@ -159,6 +159,8 @@ int check_opts(const gs_raster_opts* o) {
   if (o->reduce_mode < 0 || o->reduce_mode > 1) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
   if (o->split_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad split_threshold %d", o->split_threshold);
   if (o->reduce_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad reduce_threshold %d", o->reduce_threshold);
+  if (o->backward_order < 0 || o->backward_order > 1)
+    return fail(GS_ERR_INVALID_ARG, "bad backward_order %d", o->backward_order);
   if (o->sh_degree < 0 || o->sh_degree > kMaxShDegree) return fail(GS_ERR_INVALID_ARG, "bad sh_degree %d", o->sh_degree);
   if (!(o->t_cull >= 0.f && o->t_cull <= 1.f)) return fail(GS_ERR_INVALID_ARG, "t_cull must be in [0, 1]");
   if (o->pair_capacity < 0 || o->pair_capacity >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [0, 2^30)");
@@ -410,6 +412,7 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
                             at<float>(ws, L_G2D), opts->reduce_mode,
                             opts->reduce_threshold > 0 ? opts->reduce_threshold
                                                        : GS_REDUCE_THRESHOLD_DEFAULT,
+                            opts->backward_order,
                             num_sms(), reinterpret_cast<cudaStream_t>(stream)),
           "raster backward kernel");
   return GS_OK;

@@ -359,6 +359,46 @@ __device__ __forceinline__ void red_add9(float* dst, const float v[9]) {
   red_add_v4(dst + 8, v[8], 0.f, 0.f, 0.f);
 }
 
+// Candidate j's nine values v of this lane (frag: the lane had a fragment):
+// added directly when fewer than `threshold` lanes have one (Sec. 3.2.4),
+// else summed over the warp into part[j] and marked in `reduced`.
+template <int MODE>
+__device__ __forceinline__ void reduce_candidate(const float v[9], bool frag, int j, uint32_t rank,
+                                                 float (*part)[12], float* g2d, int threshold,
+                                                 int tslot, int lane, uint32_t& reduced) {
+  if (MODE == GS_REDUCE_NAIVE) {
+    if (frag) red_add9(g2d + (size_t)rank * 12, v);
+  } else {
+    const uint32_t active = __ballot_sync(kFull, frag);
+    if (active != 0u) {
+      if (__popc(active) < threshold) {
+        if (frag) red_add9(g2d + (size_t)rank * 12, v);
+      } else {
+        const float tot = warp_transpose_reduce9(v, lane);
+        if (tslot >= 0) part[j][tslot] = tot;
+        reduced |= 1u << j;
+      }
+    }
+  }
+}
+
+// One vector-atomic triple per reduced candidate of the group: lane j adds
+// candidate j's totals.
+template <int MODE>
+__device__ __forceinline__ void flush_reduced(float (*part)[12], const WarpRing& R, int slot,
+                                              uint32_t reduced, float* g2d, int lane) {
+  if (MODE == GS_REDUCE_NAIVE || !reduced) return;
+  __syncwarp();
+  if ((reduced >> lane) & 1u) {
+    const float4* p = reinterpret_cast<const float4*>(part[lane]);
+    float* gdst = g2d + (size_t)R.rank[slot][lane] * 12;
+    const float4 p0 = p[0], p1 = p[1], p2 = p[2];
+    red_add_v4(gdst, p0.x, p0.y, p0.z, p0.w);
+    red_add_v4(gdst + 4, p1.x, p1.y, p1.z, p1.w);
+    red_add_v4(gdst + 8, p2.x, p2.y, p2.z, p2.w);
+  }
+}
+
 // part: this warp's 32 x 12 partial sums (slots 9..11 stay zero).
 template <int COLS, int MODE>
 __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
@@ -429,34 +469,190 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
           if (NPX == 2 && hb) grad_fragment(pb, qb, y1b, y2b, a, b, c, t_cull, v);
         }
       }
-      if (MODE == GS_REDUCE_NAIVE) {
-        if (frag) red_add9(g2d + (size_t)rank * 12, v);
-      } else {
-        const uint32_t active = __ballot_sync(kFull, frag);
-        if (active != 0u) {
-          if (__popc(active) < threshold) {   // few lanes: add directly (Sec. 3.2.4)
-            if (frag) red_add9(g2d + (size_t)rank * 12, v);
-          } else {
-            const float tot = warp_transpose_reduce9(v, lane);
-            if (tslot >= 0) part[j][tslot] = tot;
-            reduced |= 1u << j;
-          }
-        }
-      }
+      reduce_candidate<MODE>(v, frag, j, rank, part, g2d, threshold, tslot, lane, reduced);
     }
-    if (MODE != GS_REDUCE_NAIVE && reduced) {
-      __syncwarp();
-      if ((reduced >> lane) & 1u) {   // lane j adds candidate j's totals
-        const float4* p = reinterpret_cast<const float4*>(part[lane]);
-        float* gdst = g2d + (size_t)R.rank[slot][lane] * 12;
-        const float4 p0 = p[0], p1 = p[1], p2 = p[2];
-        red_add_v4(gdst, p0.x, p0.y, p0.z, p0.w);
-        red_add_v4(gdst + 4, p1.x, p1.y, p1.z, p1.w);
-        red_add_v4(gdst + 8, p2.x, p2.y, p2.z, p2.w);
-      }
-    }
+    flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
     __syncwarp();   // every lane is done with the slot and `part` before they are reused
     ring_issue(R, slot, rec, ip, end, rk_next, lane);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Backward, back to front (opts backward_order = GS_BWD_BACK_TO_FRONT)
+//
+// Each pixel starts at its last fragment with T = the stored final
+// transmittance and walks towards the front: T_i = T_{i+1} / (1 - alpha_i)
+// recovers the transmittance in front of fragment i, and S, the colour of the
+// fragments behind it, gives Eq. 4 directly:
+//   dL/dalpha_i = g . (c_i T_i - S_i / (1 - alpha_i)),  S_{i-1} = S_i + T_i alpha_i c_i.
+// The fragment set is the forward's (every hit at or before the last rank).
+// ---------------------------------------------------------------------------
+struct PixelBack {
+  float S0, S1, S2, T, g0, g1, g2;
+  uint32_t end;
+};
+
+__device__ __forceinline__ void load_pixel_back(PixelBack& p, bool valid, int x, int y, int W,
+                                                int fmt, const void* state,
+                                                const uint32_t* last_in, const float* dLdC) {
+  p.S0 = p.S1 = p.S2 = 0.f;
+  p.g0 = p.g1 = p.g2 = 0.f;
+  p.T = 1.f;
+  p.end = 0;
+  if (valid) {
+    const size_t pix = (size_t)y * W + x;
+    p.T = load_state(state, fmt, pix).w;
+    p.g0 = dLdC[3 * pix]; p.g1 = dLdC[3 * pix + 1]; p.g2 = dLdC[3 * pix + 2];
+    const uint32_t l = last_in[pix];
+    p.end = (l == kNone) ? 0u : l + 1u;
+  }
+}
+
+__device__ __forceinline__ void grad_fragment_back(PixelBack& p, float q, float y1, float y2,
+                                                   const float4& a, const float4& b,
+                                                   const float4& c, float v[9]) {
+  float G, at;
+  const float alpha = frag_alpha(c.w, q, G, at);
+  const float oma = __fsub_rn(1.0f, alpha);
+  const float Ti = __fdiv_rn(p.T, oma);
+  const float wT = __fmul_rn(alpha, Ti);
+  v[5] += p.g0 * wT;
+  v[6] += p.g1 * wT;
+  v[7] += p.g2 * wT;
+  const float inv = __fdividef(1.0f, oma);
+  const float dLda = p.g0 * (c.x * Ti - p.S0 * inv) + p.g1 * (c.y * Ti - p.S1 * inv) +
+                     p.g2 * (c.z * Ti - p.S2 * inv);
+  p.S0 += wT * c.x;
+  p.S1 += wT * c.y;
+  p.S2 += wT * c.z;
+  p.T = Ti;
+  const float d_at = at < kAlphaMax ? dLda : 0.f;
+  v[8] += G * d_at;
+  const float w = at * d_at;
+  const float z1 = b.x * y2;
+  const float z0 = a.z * y1 - a.w * z1;
+  const float wz0 = w * z0, wz1 = w * z1;
+  v[0] += wz0;
+  v[1] += wz1;
+  v[2] += wz0 * z0;
+  v[3] += wz0 * z1;
+  v[4] += wz1 * z1;
+}
+
+// First index in [lo, hi) whose depth rank is >= r (hi if none): a 32-way
+// search, one coalesced probe per lane and step.
+__device__ __forceinline__ uint32_t first_rank_at_least(const uint32_t* __restrict__ pair_ranks,
+                                                        uint32_t lo, uint32_t hi, uint32_t r,
+                                                        int lane) {
+  while (hi - lo > 32u) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t p = lo + (uint32_t)lane * step;
+    const bool ge = p >= hi || __ldg(pair_ranks + p) >= r;
+    const uint32_t b = __ballot_sync(kFull, ge);
+    if (b == 0u) {
+      lo = lo + 31u * step + 1u;
+      continue;
+    }
+    const uint32_t f = (uint32_t)(__ffs(b) - 1);
+    const uint32_t nhi = min(lo + f * step, hi);
+    lo = f > 0u ? lo + (f - 1u) * step + 1u : lo;
+    hi = nhi;
+  }
+  const uint32_t p = lo + (uint32_t)lane;
+  const bool ge = p >= hi || __ldg(pair_ranks + p) >= r;
+  const uint32_t b = __ballot_sync(kFull, ge);
+  return b ? min(lo + (uint32_t)(__ffs(b) - 1), hi) : hi;
+}
+
+// Entries [glo, ghi) of group k when walking [beg, stop) backwards in 32s.
+__device__ __forceinline__ void back_group(uint32_t k, uint32_t beg, uint32_t stop, uint32_t& glo,
+                                           uint32_t& ghi) {
+  const uint64_t off = 32ull * k;
+  ghi = stop - beg > off ? stop - (uint32_t)off : beg;
+  glo = ghi - beg > 32u ? ghi - 32u : beg;
+}
+
+template <int COLS, int MODE>
+__device__ __forceinline__ void bwd_item_back(WarpRing& R, float (*part)[12],
+                                              const SplatRec* __restrict__ rec,
+                                              const uint32_t* __restrict__ pair_ranks,
+                                              uint2 range, int x0, int y0, int lane, int W, int H,
+                                              int fmt, const void* state,
+                                              const uint32_t* last_in, const float* dLdC,
+                                              float* g2d, int threshold) {
+  constexpr int NPX = COLS == 16 ? 2 : 1;
+  int x, ya;
+  bool own;
+  lane_pixels<COLS>(x0, y0, lane, x, ya, own);
+  const int yb = ya + 2;
+  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
+  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
+  const int tslot = transpose_slot(lane);
+  PixelBack pa, pb;
+  load_pixel_back(pa, own && x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
+  if (NPX == 2) {
+    load_pixel_back(pb, x < W && yb < H, x, yb, W, fmt, state, last_in, dLdC);
+  } else {
+    pb.S0 = pb.S1 = pb.S2 = 0.f;
+    pb.g0 = pb.g1 = pb.g2 = 0.f;
+    pb.T = 1.f;
+    pb.end = 0u;
+  }
+  const uint32_t warp_end = __reduce_max_sync(kFull, max(pa.end, pb.end));
+  if (warp_end == 0u) return;
+  const uint32_t beg = range.x;
+  const uint32_t stop = first_rank_at_least(pair_ranks, range.x, range.y, warp_end, lane);
+  // prologue: the last kStages groups before `stop`
+#pragma unroll
+  for (int s = 0; s < kStages; ++s) {
+    uint32_t glo, ghi;
+    back_group((uint32_t)s, beg, stop, glo, ghi);
+    const uint32_t i = glo + (uint32_t)lane;
+    const uint32_t rk = i < ghi ? __ldg(pair_ranks + i) : 0u;
+    ring_issue(R, s, rec, i, ghi, rk, lane);
+  }
+  int slot = 0;
+  for (uint32_t k = 0;; ++k, slot = (slot + 1) & (kStages - 1)) {
+    uint32_t glo, ghi;
+    back_group(k, beg, stop, glo, ghi);
+    if (glo >= ghi) break;
+    uint32_t nlo, nhi;
+    back_group(k + kStages, beg, stop, nlo, nhi);
+    const uint32_t ip = nlo + (uint32_t)lane;
+    const uint32_t rk_next = ip < nhi ? __ldg(pair_ranks + ip) : 0u;
+    cp_async_wait_group<kStages - 1>();
+    __syncwarp();
+    const uint32_t cnt = ghi - glo;
+    uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
+                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
+                                                       (float)(COLS - 1), 3.f));
+    uint32_t reduced = 0u;
+    while (m) {
+      const int j = 31 - __clz(m);   // deepest first
+      m &= ~(1u << j);
+      const uint32_t rank = R.rank[slot][j];
+      float v[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = 0.f;
+      const float4 a = R.a[slot][j];
+      const float4 b = R.b[slot][j];
+      float y1a, y2a, y1b = 0.f, y2b = 0.f, qb = 0.f;
+      const float qa = frag_q(px, pya, a, b, y1a, y2a);
+      if (NPX == 2) qb = frag_q(px, pyb, a, b, y1b, y2b);
+      const bool ha = rank < pa.end && qa <= b.y;
+      const bool hb = NPX == 2 && rank < pb.end && qb <= b.y;
+      if (ha || hb) {
+        const float4 c = R.c[slot][j];
+        if (ha) grad_fragment_back(pa, qa, y1a, y2a, a, b, c, v);
+        if (NPX == 2 && hb) grad_fragment_back(pb, qb, y1b, y2b, a, b, c, v);
+      }
+      reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
+    }
+    flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
+    __syncwarp();
+    ring_issue(R, slot, rec, ip, nhi, rk_next, lane);
   }
   cp_async_wait_all();
   __syncwarp();
@@ -468,7 +664,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     const Header* __restrict__ hdr, uint32_t* __restrict__ next,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, const void* __restrict__ state, const uint32_t* __restrict__ last_in,
-    const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold) {
+    const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold, int back) {
   __shared__ WarpRing rings[kWarps];
   __shared__ __align__(16) float s_part[kWarps][32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -484,6 +680,18 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     int block, x0, y0;
     const int cols = item_origin(items[idx], gw, block, x0, y0);
     const uint2 range = ranges[block];
+    if (back) {
+      if (cols == 16)
+        bwd_item_back<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+                                last_in, dLdC, g2d, threshold);
+      else if (cols == 8)
+        bwd_item_back<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+                               last_in, dLdC, g2d, threshold);
+      else
+        bwd_item_back<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+                               last_in, dLdC, g2d, threshold);
+      continue;
+    }
     if (cols == 16)
       bwd_item<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
                          last_in, dLdC, g2d, threshold);
@@ -597,7 +805,8 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
                               uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
                               int W, int H, int gw, int gh, float t_cull, int fmt,
                               const void* state, const uint32_t* last, const float* dLdC,
-                              float* g2d, int mode, int threshold, int num_sms, cudaStream_t st) {
+                              float* g2d, int mode, int threshold, int back, int num_sms,
+                              cudaStream_t st) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
@@ -609,13 +818,13 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_NAIVE><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold);
+        threshold, back);
   } else {
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_WARP>);
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_WARP><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold);
+        threshold, back);
   }
   return cudaGetLastError();
 }
