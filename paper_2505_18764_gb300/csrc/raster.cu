@@ -294,7 +294,6 @@ __device__ __forceinline__ int transpose_slot(int lane) {
 struct PixelBwd {
   float Cp0, Cp1, Cp2, T, g0, g1, g2;
   uint32_t end;   // depth rank after the pixel's last fragment
-  bool done;
 };
 
 __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, int y, int W,
@@ -312,14 +311,16 @@ __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, i
     const uint32_t l = last_in[pix];
     p.end = (l == kNone) ? 0u : l + 1u;
   }
-  p.done = p.end == 0;
 }
 
 // One fragment of Procedure 1 plus the chain rule to the 2D parameters; the
-// nine values are added into v.
+// nine values are added into v.  The pixel's fragments are exactly the hits
+// below its end rank: the forward stopped after the fragment that took T
+// under t_cull, and the same arithmetic in the same order gives the same T
+// here, so Procedure 1's cull test needs no second evaluation.
 __device__ __forceinline__ void grad_fragment(PixelBwd& p, float q, float y1, float y2,
                                               const float4& a, const float4& b, const float4& c,
-                                              float t_cull, float v[9]) {
+                                              float v[9]) {
   float G, at;
   const float alpha = frag_alpha(c.w, q, G, at);
   const float oma = __fsub_rn(1.0f, alpha);
@@ -336,7 +337,6 @@ __device__ __forceinline__ void grad_fragment(PixelBwd& p, float q, float y1, fl
   p.Cp1 -= wT * c.y;
   p.Cp2 -= wT * c.z;
   p.T = next_T(p.T, alpha);
-  if (p.T < t_cull) p.done = true;
   // alpha = min(0.99, o G): no gradient through the clamp
   const float d_at = at < kAlphaMax ? dLda : 0.f;
   v[8] += G * d_at;
@@ -404,8 +404,8 @@ template <int COLS, int MODE>
 __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
                                          const SplatRec* __restrict__ rec,
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
-                                         int x0, int y0, int lane, int W, int H, float t_cull,
-                                         int fmt, const void* state, const uint32_t* last_in,
+                                         int x0, int y0, int lane, int W, int H, int fmt,
+                                         const void* state, const uint32_t* last_in,
                                          const float* dLdC, float* g2d, int threshold) {
   constexpr int NPX = COLS == 16 ? 2 : 1;
   int x, ya;
@@ -424,7 +424,6 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
     pb.g0 = pb.g1 = pb.g2 = 0.f;
     pb.T = 1.f;
     pb.end = 0u;
-    pb.done = true;
   }
   // depth ranks >= this contribute nowhere in the footprint
   const uint32_t warp_end = __reduce_max_sync(kFull, max(pa.end, pb.end));
@@ -437,7 +436,6 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
     const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
     cp_async_wait_group<kStages - 1>();
     __syncwarp();
-    if (__all_sync(kFull, pa.done && pb.done)) break;
     if (R.rank[slot][0] >= warp_end) break;   // ranks ascend along the list
     const uint32_t cnt = min(32u, end - gs);
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
@@ -451,25 +449,19 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
       float v[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) v[q] = 0.f;
-      bool frag = false;
-      if (!(pa.done && pb.done)) {
-        const float4 a = R.a[slot][j];
-        const float4 b = R.b[slot][j];
-        float y1a, y2a, y1b = 0.f, y2b = 0.f, qb = 0.f;
-        const float qa = frag_q(px, pya, a, b, y1a, y2a);
-        if (NPX == 2) qb = frag_q(px, pyb, a, b, y1b, y2b);
-        if (rank >= pa.end) pa.done = true;   // past this pixel's last fragment
-        if (rank >= pb.end) pb.done = true;
-        const bool ha = !pa.done && qa <= b.y;
-        const bool hb = NPX == 2 && !pb.done && qb <= b.y;
-        if (ha || hb) {
-          const float4 c = R.c[slot][j];
-          frag = true;
-          if (ha) grad_fragment(pa, qa, y1a, y2a, a, b, c, t_cull, v);
-          if (NPX == 2 && hb) grad_fragment(pb, qb, y1b, y2b, a, b, c, t_cull, v);
-        }
+      const float4 a = R.a[slot][j];
+      const float4 b = R.b[slot][j];
+      float y1a, y2a, y1b = 0.f, y2b = 0.f, qb = 0.f;
+      const float qa = frag_q(px, pya, a, b, y1a, y2a);
+      if (NPX == 2) qb = frag_q(px, pyb, a, b, y1b, y2b);
+      const bool ha = rank < pa.end && qa <= b.y;
+      const bool hb = NPX == 2 && rank < pb.end && qb <= b.y;
+      if (ha || hb) {
+        const float4 c = R.c[slot][j];
+        if (ha) grad_fragment(pa, qa, y1a, y2a, a, b, c, v);
+        if (NPX == 2 && hb) grad_fragment(pb, qb, y1b, y2b, a, b, c, v);
       }
-      reduce_candidate<MODE>(v, frag, j, rank, part, g2d, threshold, tslot, lane, reduced);
+      reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
     }
     flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
     __syncwarp();   // every lane is done with the slot and `part` before they are reused
@@ -693,13 +685,13 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
       continue;
     }
     if (cols == 16)
-      bwd_item<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+      bwd_item<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                          last_in, dLdC, g2d, threshold);
     else if (cols == 8)
-      bwd_item<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+      bwd_item<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                         last_in, dLdC, g2d, threshold);
     else
-      bwd_item<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, state,
+      bwd_item<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                         last_in, dLdC, g2d, threshold);
   }
 }
