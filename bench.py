@@ -34,7 +34,7 @@ METRIC = "fwd+bwd ms/view, splat-frags/s at 3M/1256x828, FP16 vs FP32 state; p99
 WORKLOAD = "mipnerf360-shaped synthetic scene, 3.0M splats SH3, 1256x828, L1 loss, fwd+bwd"
 N_SPLATS = 3_000_000
 STAGES = ("project", "sort", "bin", "blend_fwd", "loss", "blend_bwd", "project_bwd")
-KERNELS_PER_STAGE = {"project": 1, "sort": 4, "bin": None, "blend_fwd": 1, "loss": 1,
+KERNELS_PER_STAGE = {"project": 1, "sort": 5, "bin": None, "blend_fwd": 1, "loss": 1,
                      "blend_bwd": 2, "project_bwd": 1}   # bin: 2 + pair-sort passes
 # Nominal FP32 rate (SM count x FP32 lanes x 2 flop x max SM clock): raster stages are
 # plain FP32 ALU work, for which the measured peaks carry no figure.
@@ -233,8 +233,9 @@ def run_ours(args, rank, world, local_rank):
     P_live = cnt["live_pairs"]
     npix = H * W
     passes = ws.c.pair_passes
-    # bin: count, emit, pair-sort passes, ranges, item order; blend_bwd: item reorder + raster
-    kernels_per_step = 1 + 4 + (2 + passes + 2) + 1 + 1 + 2 + 1
+    # sort: epoch + 4 passes; bin: count, chunk setup, emit, pair-sort passes, ranges, item
+    # order; blend_bwd: item reorder + raster
+    kernels_per_step = 1 + 5 + (3 + passes + 2) + 1 + 1 + 2 + 1
     K_sh = 16
 
     # algorithmic bytes (HBM-bound stages) and flops (raster stages) per launch
@@ -310,6 +311,7 @@ def run_ours(args, rank, world, local_rank):
                              last, dl, loss, grads, ws)
         res["reduction_ablation"] = run_ablation(gs, torch, ws, ccam, state32, last, dl, stream, F)
         res["back_to_front"] = run_backward_order(gs, torch, ws, ccam, state32, last, dl, stream)
+        res["memory_efficiency"] = run_chunked(args, gs, torch, scene, ccam, target, dev, stream)
         if not args.no_training:
             res["training"] = run_training(args, dev)
         res["clocks"] = clk
@@ -362,6 +364,51 @@ def run_backward_order(gs, torch, ws, ccam, state, last, dl, stream, reps=10):
         torch.cuda.synchronize()
         out[order + "_ms"] = round(float(np.median([ev[2 * k].elapsed_time(ev[2 * k + 1])
                                                     for k in range(reps)])), 4)
+    return out
+
+
+def run_chunked(args, gs, torch, scene, ccam, target, dev, stream, caps=(1 << 20, 1 << 18)):
+    """The same view in the memory-efficiency mode: a small fixed pair capacity,
+    the depth order binned and rasterized in chunks that fit it.  Reports time
+    per view (fwd + bwd through gs_raster_forward / gs_raster_backward), chunk
+    count and workspace bytes against the default single-pass workspace."""
+    W, H = ccam.width, ccam.height
+    o_def = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4)
+    out = dict(default_workspace_bytes=gs.Workspace.required_bytes(scene.n, W, H, o_def),
+               default_pair_capacity=max(16 * scene.n, 1 << 22), runs=[])
+    grads = gs.zero_grads(scene)
+    for cap in caps:
+        o = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4, chunked=True,
+                          pair_capacity=cap)
+        ws = gs.Workspace(scene.n, W, H, o, device=dev)
+        image = torch.empty((H, W, 3), device=dev)
+        state = gs.alloc_state(H, W, "fp32", dev)
+        last = torch.empty((H, W), dtype=torch.int32, device=dev)
+        dl = torch.empty((H, W, 3), device=dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def step():
+            gs.project(ws, scene, ccam, o, stream)
+            gs.sort(ws, stream)
+            gs.raster_forward(ws, ccam, o, image, state, last, None, stream=stream)
+            gs.loss(image, target, "l1", dl, loss, stream)
+            gs.raster_backward(ws, scene, ccam, o, state, last, dl, grads, stream)
+
+        step()
+        torch.cuda.synchronize(dev)
+        K = 5
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        gs.check_status(ws, stream)
+        out["runs"].append(dict(pair_capacity=cap, chunks=int(ws.c.n_chunks),
+                                workspace_bytes=int(ws.nbytes),
+                                pair_buffer_bytes=4 * 4 * cap,
+                                ms_per_view=round(a.elapsed_time(b) / K, 4)))
+        del ws
     return out
 
 

@@ -108,7 +108,11 @@ typedef struct gs_raster_opts {
                                0 = default (GS_SPLIT_THRESHOLD_DEFAULT).  Results do not depend
                                on it. */
   int32_t backward_order;   /* GS_BWD_* */
-  int32_t reserved;
+  int32_t chunked;          /* memory-efficiency mode (1): the view is binned and rasterized in
+                               chunks of the depth order whose pairs fit the pair capacity (at
+                               least twice the block count), each pixel carrying its state from
+                               one chunk to the next; only through gs_raster_forward and
+                               gs_raster_backward, front to back.  Fixed at gs_workspace_init. */
   int64_t pair_capacity;    /* (splat, 16x16 block) pairs the workspace holds; 0 = 16 per splat */
 } gs_raster_opts;
 
@@ -117,11 +121,11 @@ typedef struct gs_raster_opts {
 typedef struct gs_workspace {
   void* base;      /* device memory, >= gs_workspace_size bytes, 256-B aligned */
   size_t bytes;
-  int32_t n_cap, width_cap, height_cap, reserved;
+  int32_t n_cap, width_cap, height_cap, chunked;   /* chunked: opts->chunked at init */
   int64_t pair_cap;
   /* bound by gs_project (read by the later calls) */
   int32_t n, width, height, sh_degree;
-  int32_t state_format, clamp01, pair_passes, sorted_in_b;
+  int32_t state_format, clamp01, pair_passes, n_chunks;   /* n_chunks: of the last forward */
   uint64_t layout[24]; /* byte offsets of the internal arrays */
 } gs_workspace;
 

@@ -33,6 +33,7 @@ class RasterOpts:
     pair_capacity: int = 0
     split_threshold: int = 0
     backward_order: str = "front_to_back"
+    chunked: bool = False
 
     def to_c(self) -> _lib.GsRasterOpts:
         o = _lib.GsRasterOpts()
@@ -44,6 +45,7 @@ class RasterOpts:
         o.pair_capacity = int(self.pair_capacity)
         o.split_threshold = int(self.split_threshold)
         o.backward_order = BACKWARD_ORDERS[self.backward_order]
+        o.chunked = int(bool(self.chunked))
         return o
 
 

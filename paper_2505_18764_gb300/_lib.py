@@ -41,16 +41,16 @@ class GsCamera(Structure):
 class GsRasterOpts(Structure):
     _fields_ = [("state_format", c_int32), ("reduce_mode", c_int32),
                 ("reduce_threshold", c_int32), ("sh_degree", c_int32), ("t_cull", c_float),
-                ("split_threshold", c_int32), ("backward_order", c_int32), ("reserved", c_int32),
+                ("split_threshold", c_int32), ("backward_order", c_int32), ("chunked", c_int32),
                 ("pair_capacity", c_int64)]
 
 
 class GsWorkspace(Structure):
     _fields_ = [("base", c_void_p), ("bytes", c_size_t), ("n_cap", c_int32),
-                ("width_cap", c_int32), ("height_cap", c_int32), ("reserved", c_int32),
+                ("width_cap", c_int32), ("height_cap", c_int32), ("chunked", c_int32),
                 ("pair_cap", c_int64), ("n", c_int32), ("width", c_int32), ("height", c_int32),
                 ("sh_degree", c_int32), ("state_format", c_int32), ("clamp01", c_int32),
-                ("pair_passes", c_int32), ("sorted_in_b", c_int32), ("layout", c_uint64 * 24)]
+                ("pair_passes", c_int32), ("n_chunks", c_int32), ("layout", c_uint64 * 24)]
 
 
 class GsSceneRef(Structure):

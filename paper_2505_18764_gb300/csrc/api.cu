@@ -24,23 +24,25 @@ cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, ui
                                  uint32_t, uint32_t*, int, int, cudaStream_t);
 cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
-cudaError_t launch_bin(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*, Header*,
-                       unsigned long long*, const uint32_t*, uint32_t*, uint2*, uint32_t*, uint32_t*,
-                       uint32_t*, uint32_t, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_bin_count(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*,
+                             Header*, unsigned long long*, const uint32_t*, uint32_t*, uint2*,
+                             uint32_t, int, int, int, cudaStream_t);
+cudaError_t launch_bin_chunk(const uint32_t*, const uint2*, const SplatRec*, Header*, uint32_t*,
+                             uint32_t, uint32_t, uint32_t, int, uint2*, uint32_t*, uint32_t*, int,
+                             int, int, int, cudaStream_t);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, int, cudaStream_t);
 cudaError_t launch_block_order(const uint2*, int, uint32_t, uint32_t*, Header*, cudaStream_t);
 cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint32_t*, uint32_t*,
                               const uint32_t*, const SplatRec*, int, int, int, int, float, int,
-                              float*, void*, uint32_t*, uint32_t*, int, cudaStream_t);
+                              float*, void*, uint32_t*, uint32_t*, int, int, cudaStream_t);
 cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, uint32_t*,
                               const Header*, uint32_t*, const uint32_t*, const SplatRec*, int, int,
                               int, int, float, int, const void*, const uint32_t*, const float*,
-                              float*, int, int, int, int, cudaStream_t);
+                              float*, int, int, int, float4*, int, int, int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
                         cudaStream_t);
 size_t sort_tiles(size_t n);
 size_t bin_tiles(size_t n);
-size_t emit_chunks(size_t pairs);
 
 namespace {
 
@@ -96,7 +98,7 @@ enum Slot {
   L_G2D,         // [n][12] backward accumulators by depth rank
   L_OFFSETS,     // [n] first pair index of each depth rank
   L_BOXES,       // [n] uint2 block box of each depth rank
-  L_CHUNKS,      // [pair_cap / 2048 + 1] first depth rank of each emission chunk
+  L_CHUNK_STATE, // [width_cap * height_cap] float4 (C', T) between chunks (memory-efficiency mode)
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
   L_ORDER,       // [16 blocks_cap] u32 raster work items (warp footprints), longest lists first
@@ -119,8 +121,8 @@ int blocks_of(int w, int h, int& gw, int& gh) {
   return gw * gh;
 }
 
-bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint64_t* off,
-                    size_t* total) {
+bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, int chunked,
+                    uint64_t* off, size_t* total) {
   int gw, gh;
   const size_t blocks = blocks_of(w_cap, h_cap, gw, gh);
   const size_t st_tiles = std::max(sort_tiles(n_cap), sort_tiles(pair_cap)) + 1;
@@ -135,7 +137,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, uint6
   sz[L_OFFSETS] = n_cap * 4;
   sz[L_BOXES_ID] = n_cap * 8;
   sz[L_BOXES] = n_cap * 8;
-  sz[L_CHUNKS] = (emit_chunks(pair_cap) + 1) * 4;
+  sz[L_CHUNK_STATE] = chunked ? (size_t)w_cap * h_cap * 16 : 0;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
   sz[L_ORDER] = sz[L_ITEM_COST] = sz[L_BWD_ITEMS] = blocks * 16 * 4;
@@ -161,6 +163,9 @@ int check_opts(const gs_raster_opts* o) {
   if (o->reduce_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad reduce_threshold %d", o->reduce_threshold);
   if (o->backward_order < 0 || o->backward_order > 1)
     return fail(GS_ERR_INVALID_ARG, "bad backward_order %d", o->backward_order);
+  if (o->chunked < 0 || o->chunked > 1) return fail(GS_ERR_INVALID_ARG, "bad chunked %d", o->chunked);
+  if (o->chunked && o->backward_order != GS_BWD_FRONT_TO_BACK)
+    return fail(GS_ERR_INVALID_ARG, "the memory-efficiency mode walks front to back only");
   if (o->sh_degree < 0 || o->sh_degree > kMaxShDegree) return fail(GS_ERR_INVALID_ARG, "bad sh_degree %d", o->sh_degree);
   if (!(o->t_cull >= 0.f && o->t_cull <= 1.f)) return fail(GS_ERR_INVALID_ARG, "t_cull must be in [0, 1]");
   if (o->pair_capacity < 0 || o->pair_capacity >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [0, 2^30)");
@@ -218,7 +223,7 @@ int gs_workspace_size(int32_t n_cap, int32_t width_cap, int32_t height_cap,
   const int64_t pcap = opts->pair_capacity ? opts->pair_capacity : default_pair_cap(n_cap);
   if (pcap >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "pair capacity must be < 2^30");
   uint64_t off[L_END];
-  compute_layout(n_cap, width_cap, height_cap, pcap, off, bytes);
+  compute_layout(n_cap, width_cap, height_cap, pcap, opts->chunked, off, bytes);
   return GS_OK;
 }
 
@@ -242,7 +247,8 @@ int gs_workspace_init(gs_workspace* ws, void* device_base, size_t bytes, int32_t
   ws->pair_cap = opts->pair_capacity ? opts->pair_capacity : default_pair_cap(n_cap);
   static_assert(L_END <= 24, "layout table too small");
   size_t total = 0;
-  compute_layout(n_cap, width_cap, height_cap, ws->pair_cap, ws->layout, &total);
+  compute_layout(n_cap, width_cap, height_cap, ws->pair_cap, opts->chunked, ws->layout, &total);
+  ws->chunked = opts->chunked;
   // Header, epoch and all look-back words start at zero (a zero word never
   // carries a valid tag's flag); ordered before later work on `stream`.
   GS_CUDA(cudaMemsetAsync(device_base, 0, ws->layout[L_SCAN + 1],
@@ -287,9 +293,12 @@ int gs_sort(gs_workspace* ws, gs_stream_t stream) {
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Header* hdr = at<Header>(ws, L_HDR);
-  const uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
+  uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
   unsigned long long* status = at<unsigned long long>(ws, L_STATUS);
   const int grid_cap = num_sms() * kPersistentPerSm;
+  // a sort may repeat without a new projection: fresh tile counters and look-back tags
+  GS_CUDA(cudaMemsetAsync(&hdr->tile_counter[0], 0, 4 * sizeof(uint32_t), st), "sort counters");
+  GS_CUDA(launch_bump_epoch(epoch, st), "epoch kernel");
   uint32_t* bufs_k[2] = {at<uint32_t>(ws, L_KA), at<uint32_t>(ws, L_KB)};
   uint32_t* bufs_v[2] = {at<uint32_t>(ws, L_VA), at<uint32_t>(ws, L_VB)};
   for (int pass = 0; pass < 4; ++pass) {
@@ -303,7 +312,6 @@ int gs_sort(gs_workspace* ws, gs_stream_t stream) {
                                  (uint32_t)pass, &hdr->status, pass == 0, grid_cap, st),
             "depth sort pass");
   }
-  ws->sorted_in_b = 1;  // four passes: a, b, a, b
   return GS_OK;
 }
 
@@ -319,22 +327,37 @@ static int check_bound(gs_workspace* ws, const gs_camera* cam, const gs_raster_o
   return GS_OK;
 }
 
-int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, gs_stream_t stream) {
-  int rc = check_bound(ws, cam, opts);
-  if (rc) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+namespace {
+
+// Binning, first pass: records into depth order, box pair counts, their scan.
+int bin_count_stage(gs_workspace* ws, cudaStream_t st) {
   Header* hdr = at<Header>(ws, L_HDR);
-  const uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
+  const int grid_cap = num_sms() * kPersistentPerSm;
+  GS_CUDA(cudaMemsetAsync(&hdr->tile_counter[8], 0, sizeof(uint32_t), st), "bin counter");
+  GS_CUDA(launch_bin_count(at<uint32_t>(ws, L_VB), at<SplatRec>(ws, L_REC),
+                           at<uint2>(ws, L_BOXES_ID), at<SplatRec>(ws, L_REC_SORTED),
+                           at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN),
+                           at<uint32_t>(ws, L_EPOCH), at<uint32_t>(ws, L_OFFSETS),
+                           at<uint2>(ws, L_BOXES), (uint32_t)ws->pair_cap, ws->chunked, ws->n,
+                           grid_cap, st),
+          "bin count kernel");
+  return GS_OK;
+}
+
+// Binning of chunk k (the only chunk without the memory-efficiency mode):
+// emission, the pair sort by block, block ranges and raster work items.
+int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                    uint32_t k, uint32_t B, cudaStream_t st) {
+  Header* hdr = at<Header>(ws, L_HDR);
+  uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int grid_cap = num_sms() * kPersistentPerSm;
-  GS_CUDA(launch_bin(at<uint32_t>(ws, L_VB), at<SplatRec>(ws, L_REC), at<uint2>(ws, L_BOXES_ID),
-                     at<SplatRec>(ws, L_REC_SORTED),
-                     at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN), epoch,
-                     at<uint32_t>(ws, L_OFFSETS), at<uint2>(ws, L_BOXES), at<uint32_t>(ws, L_CHUNKS),
-                     at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PVA), (uint32_t)ws->pair_cap,
-                     gw, gh, ws->pair_passes, ws->n, grid_cap, st),
-          "bin kernel");
+  GS_CUDA(launch_bin_chunk(at<uint32_t>(ws, L_OFFSETS), at<uint2>(ws, L_BOXES),
+                           at<SplatRec>(ws, L_REC_SORTED), hdr, epoch, k, B, (uint32_t)ws->pair_cap,
+                           ws->chunked, at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_PKA),
+                           at<uint32_t>(ws, L_PVA), gw, gh, ws->pair_passes, grid_cap, st),
+          "bin emit kernel");
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
   uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};
   for (int q = 0; q < ws->pair_passes; ++q) {
@@ -359,13 +382,28 @@ int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, g
   return GS_OK;
 }
 
-int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
-                     float* image, void* state, uint32_t* last, uint32_t* n_contrib,
-                     gs_stream_t stream) {
-  int rc = check_bound(ws, cam, opts);
-  if (rc) return rc;
-  const size_t npix = (size_t)cam->width * cam->height;
-  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
+// Chunks of the bound view in the memory-efficiency mode (synchronises `st`
+// to read the view's pair count) and their pair budget B.
+int count_chunks(gs_workspace* ws, const gs_camera* cam, cudaStream_t st, uint32_t* n_chunks,
+                 uint32_t* B) {
+  int gw, gh;
+  const int64_t blocks = blocks_of(cam->width, cam->height, gw, gh);
+  if (ws->pair_cap < 2 * blocks)
+    return fail(GS_ERR_INVALID_ARG,
+                "memory-efficiency mode needs a pair capacity of at least twice the block count (%lld)",
+                (long long)(2 * blocks));
+  uint32_t total = 0;
+  GS_CUDA(cudaMemcpyAsync(&total, &at<Header>(ws, L_HDR)->pairs_wanted, 4, cudaMemcpyDeviceToHost,
+                          st), "pair count copy");
+  GS_CUDA(cudaStreamSynchronize(st), "pair count sync");
+  *B = (uint32_t)(ws->pair_cap - blocks);
+  *n_chunks = total == 0 ? 1u : (uint32_t)((total + (uint64_t)*B - 1) / *B);
+  return GS_OK;
+}
+
+int raster_fwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                     float* image, void* state, uint32_t* last, uint32_t* n_contrib, int resume,
+                     cudaStream_t st) {
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
@@ -375,31 +413,14 @@ int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
                             at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, image, state, last, n_contrib,
-                            num_sms(), reinterpret_cast<cudaStream_t>(stream)),
+                            resume, num_sms(), st),
           "raster forward kernel");
   return GS_OK;
 }
 
-int gs_raster_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
-                      float* image, void* state, uint32_t* last, uint32_t* n_contrib,
-                      gs_stream_t stream) {
-  int rc = check_bound(ws, cam, opts);
-  if (rc) return rc;
-  const size_t npix = (size_t)cam->width * cam->height;
-  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
-  rc = gs_bin(ws, cam, opts, stream);
-  if (rc) return rc;
-  return gs_blend_forward(ws, cam, opts, image, state, last, n_contrib, stream);
-}
-
-int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
-                      const void* state, const uint32_t* last, const float* dL_dimage,
-                      gs_stream_t stream) {
-  int rc = check_bound(ws, cam, opts);
-  if (rc) return rc;
-  const size_t npix = (size_t)cam->width * cam->height;
-  if (npix > 0 && (!state || !last || !dL_dimage))
-    return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
+int raster_bwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                     const void* state, const uint32_t* last, const float* dL_dimage,
+                     int chunk_in, int chunk_out, cudaStream_t st) {
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
@@ -412,10 +433,80 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
                             at<float>(ws, L_G2D), opts->reduce_mode,
                             opts->reduce_threshold > 0 ? opts->reduce_threshold
                                                        : GS_REDUCE_THRESHOLD_DEFAULT,
-                            opts->backward_order,
-                            num_sms(), reinterpret_cast<cudaStream_t>(stream)),
+                            opts->backward_order, at<float4>(ws, L_CHUNK_STATE), chunk_in,
+                            chunk_out, num_sms(), st),
           "raster backward kernel");
   return GS_OK;
+}
+
+}  // namespace
+
+int gs_bin(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts, gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (ws->chunked)
+    return fail(GS_ERR_INVALID_ARG,
+                "memory-efficiency mode: bin and blend through gs_raster_forward / gs_raster_backward");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  rc = bin_count_stage(ws, st);
+  if (rc) return rc;
+  return bin_chunk_stage(ws, cam, opts, 0u, 0u, st);
+}
+
+int gs_blend_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                     float* image, void* state, uint32_t* last, uint32_t* n_contrib,
+                     gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (ws->chunked)
+    return fail(GS_ERR_INVALID_ARG, "memory-efficiency mode: use gs_raster_forward");
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
+  return raster_fwd_stage(ws, cam, opts, image, state, last, n_contrib, 0,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gs_raster_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                      float* image, void* state, uint32_t* last, uint32_t* n_contrib,
+                      gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!ws->chunked) {
+    rc = gs_bin(ws, cam, opts, stream);
+    if (rc) return rc;
+    return gs_blend_forward(ws, cam, opts, image, state, last, n_contrib, stream);
+  }
+  // memory-efficiency mode: chunks of the depth order, front to back, each
+  // pixel resuming from the state the previous chunk stored
+  rc = bin_count_stage(ws, st);
+  if (rc) return rc;
+  uint32_t n_chunks = 0, B = 0;
+  rc = count_chunks(ws, cam, st, &n_chunks, &B);
+  if (rc) return rc;
+  ws->n_chunks = (int32_t)n_chunks;
+  for (uint32_t k = 0; k < n_chunks; ++k) {
+    rc = bin_chunk_stage(ws, cam, opts, k, B, st);
+    if (!rc) rc = raster_fwd_stage(ws, cam, opts, image, state, last, n_contrib, k > 0, st);
+    if (rc) return rc;
+  }
+  return GS_OK;
+}
+
+int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                      const void* state, const uint32_t* last, const float* dL_dimage,
+                      gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (ws->chunked)
+    return fail(GS_ERR_INVALID_ARG, "memory-efficiency mode: use gs_raster_backward");
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last || !dL_dimage))
+    return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
+  return raster_bwd_stage(ws, cam, opts, state, last, dL_dimage, 0, 0,
+                          reinterpret_cast<cudaStream_t>(stream));
 }
 
 int gs_project_backward(gs_workspace* ws, const float* means, const float* scales,
@@ -449,7 +540,24 @@ int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales
   if (n > 0 && (!means || !scales || !quats || !opacities || !sh || !d_means || !d_scales ||
                 !d_quats || !d_opacities || !d_sh))
     return fail(GS_ERR_INVALID_ARG, "null parameter or gradient pointer");
-  rc = gs_blend_backward(ws, cam, opts, state, last, dL_dimage, stream);
+  if (!ws->chunked) {
+    rc = gs_blend_backward(ws, cam, opts, state, last, dL_dimage, stream);
+  } else {
+    // memory-efficiency mode: the chunks again, front to back, (C', T) carried
+    // between them; the pair buffers hold one chunk, so each is binned anew
+    const size_t npix = (size_t)cam->width * cam->height;
+    if (npix > 0 && (!state || !last || !dL_dimage))
+      return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
+    const uint32_t n_chunks = (uint32_t)ws->n_chunks;
+    if (n_chunks == 0) return fail(GS_ERR_INVALID_ARG, "gs_raster_forward must run first");
+    int gw, gh;
+    const uint32_t B = (uint32_t)(ws->pair_cap - blocks_of(cam->width, cam->height, gw, gh));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (uint32_t k = 0; k < n_chunks && !rc; ++k) {
+      rc = bin_chunk_stage(ws, cam, opts, k, B, st);
+      if (!rc) rc = raster_bwd_stage(ws, cam, opts, state, last, dL_dimage, k > 0, k + 1 < n_chunks, st);
+    }
+  }
   if (rc) return rc;
   return gs_project_backward(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
                              d_scales, d_quats, d_opacities, d_sh, stream);

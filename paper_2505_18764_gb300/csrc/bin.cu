@@ -9,13 +9,18 @@
 //      accumulators, counts its blocks and scans the counts across tiles with a
 //      decoupled look-back (tagged 64-bit status words, bounded waits), giving
 //      every rank its first pair index;
-//   emit: each CTA writes whole chunks of 2048 consecutive pairs (a binary
-//      search over the chunk's ranks in shared memory finds each pair's
-//      splat), so the work is even even though the nearest splats are the
+//   emit: each CTA writes whole runs of 2048 consecutive pairs (binary searches
+//      over the ranks' first pair indices find the run's splats, then each
+//      pair's), so the work is even even though the nearest splats are the
 //      largest on screen; it also accumulates the 8-bit digit histograms of the
 //      block ids that the stable pair sort by block needs (depth order survives
 //      within a block).
-// Pairs beyond the capacity are not written; the shortfall is recorded.
+// The pairs a view needs may exceed the workspace's capacity.  Normally the
+// shortfall is recorded and the view fails with GS_ERR_CAPACITY.  In the
+// memory-efficiency mode the depth ranks are cut into chunks whose pairs fit
+// (chunk k holds the splats whose first pair index lies in [k B, (k + 1) B),
+// B = capacity - blocks, so no chunk exceeds the capacity) and each chunk is
+// emitted, sorted and rasterized in turn, front to back.
 #include "common.cuh"
 
 namespace gsr {
@@ -34,8 +39,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
     const uint2* __restrict__ boxes_by_id, SplatRec* __restrict__ rec_sorted,
     float4* __restrict__ g2d, Header* __restrict__ hdr,
     unsigned long long* __restrict__ scan_status, const uint32_t* __restrict__ epoch,
-    uint32_t* __restrict__ offsets, uint2* __restrict__ boxes, uint32_t* __restrict__ chunk_rank,
-    uint32_t pair_cap) {
+    uint32_t* __restrict__ offsets, uint2* __restrict__ boxes, uint32_t pair_cap, int chunked) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_cnt[kBinTile];
   __shared__ uint32_t s_warp[kBinThreads / 32];
@@ -44,7 +48,6 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
   const uint32_t V = hdr->visible;
   const uint32_t ntiles = (V + kBinTile - 1) / kBinTile;
   const uint32_t tag = *epoch;
-  const uint32_t chunk_cap = (pair_cap + kEmitChunk - 1) / kEmitChunk;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter[8], 1u);
     __syncthreads();
@@ -140,54 +143,100 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
         const unsigned long long want = excl + total;
         hdr->pairs_wanted = (uint32_t)min(want, (unsigned long long)0xFFFFFFFFu);
         hdr->pairs = (uint32_t)min(want, (unsigned long long)pair_cap);
-        if (want > pair_cap) atomicOr(&hdr->status, kStatusCapacity);
+        if (want > pair_cap && !chunked) atomicOr(&hdr->status, kStatusCapacity);
       }
     }
     __syncthreads();
-    // global exclusive offsets; each emission chunk boundary c * kEmitChunk lies in
-    // exactly one rank's pair range, and that rank records itself for the chunk
+    // global exclusive offsets (saturated at 2^32 - 1)
     unsigned long long run = s_off + wbefore + x - sum;
 #pragma unroll
     for (int k = 0; k < kBinItems; ++k) {
       const uint32_t r = base + tid * kBinItems + k;
-      if (r < V) {
-        // saturated: only pairs below the capacity (< 2^30) are ever emitted
-        offsets[r] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
-        if (c4[k]) {
-          unsigned long long c = (run + kEmitChunk - 1) / kEmitChunk;
-          const unsigned long long end = run + c4[k];
-          for (; c * kEmitChunk < end && c < chunk_cap; ++c) chunk_rank[c] = r;
-        }
-      }
+      if (r < V) offsets[r] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
       run += c4[k];
     }
     __syncthreads();
   }
 }
 
-// Pass 2: every CTA writes whole chunks of kEmitChunk consecutive pairs, so the
-// work is even however the pairs are spread over splats.
+// Last rank r in [0, V) with offsets[r] <= p (offsets ascend; offsets[0] = 0).
+__device__ __forceinline__ uint32_t rank_of_pair(const uint32_t* __restrict__ offsets, uint32_t V,
+                                                 uint32_t p) {
+  uint32_t lo = 0, hi = V;   // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (offsets[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Chunk k of the view: pair indices [pair_base, pair_base + pairs) and the
+// per-chunk state the emission and the pair sort start from.  Without the
+// memory-efficiency mode there is one chunk, the first `capacity` pairs.  It
+// also advances the epoch: the pair sort's look-back words of any earlier
+// chunk or binning then carry a stale tag and are never taken for this one's.
+__global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __restrict__ offsets,
+                                                          Header* __restrict__ hdr,
+                                                          uint32_t* __restrict__ epoch, uint32_t k,
+                                                          uint32_t B, uint32_t pair_cap,
+                                                          int chunked, uint2* __restrict__ ranges,
+                                                          int nblocks) {
+  __shared__ uint32_t s_lo, s_hi;
+  const uint32_t V = hdr->visible, total = hdr->pairs_wanted;
+  if (threadIdx.x == 0) {
+    uint32_t lo = 0, hi = min(total, pair_cap);
+    if (chunked) {
+      // first rank whose first pair index is >= t
+      auto first_at = [&](unsigned long long t) -> uint32_t {
+        if (t >= total) return total;
+        uint32_t a = 0, b = V;   // answer in [a, b]
+        while (a < b) {
+          const uint32_t mid = a + (b - a) / 2;
+          if (offsets[mid] >= t) b = mid; else a = mid + 1;
+        }
+        return a < V ? offsets[a] : total;
+      };
+      lo = first_at((unsigned long long)k * B);
+      hi = first_at((unsigned long long)(k + 1) * B);
+    }
+    s_lo = lo;
+    s_hi = hi;
+    *epoch += 1u;
+    hdr->pair_base = lo;
+    hdr->pairs = hi - lo;
+    hdr->live_pairs = 0;
+    for (int q = 4; q < 8; ++q) hdr->tile_counter[q] = 0;
+  }
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&hdr->pair_hist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) ranges[i] = make_uint2(0, 0);
+}
+
+// Pass 2: every CTA writes whole runs of kEmitChunk consecutive pairs of the
+// chunk, so the work is even however the pairs are spread over splats.
 __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
     const uint32_t* __restrict__ offsets, const uint2* __restrict__ boxes,
-    const uint32_t* __restrict__ chunk_rank, const SplatRec* __restrict__ rec_sorted,
-    Header* __restrict__ hdr, uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals,
-    int gw, int gh, int pair_passes) {
+    const SplatRec* __restrict__ rec_sorted, Header* __restrict__ hdr,
+    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, int gw, int gh,
+    int pair_passes) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   __shared__ uint2 s_box[kEmitChunk + 1];
   __shared__ uint32_t s_hist[4][256];
+  __shared__ uint32_t s_r0, s_r1;
   const int tid = threadIdx.x;
   for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
-  const uint32_t P = hdr->pairs, V = hdr->visible;
-  const uint32_t nchunks = (P + kEmitChunk - 1) / kEmitChunk;
+  const uint32_t P = hdr->pairs, V = hdr->visible, pbase = hdr->pair_base;
+  const uint32_t nruns = (P + kEmitChunk - 1) / kEmitChunk;
   uint32_t live = 0;
-  for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const uint32_t p0 = c * kEmitChunk;
-    const uint32_t p1 = min(P, p0 + kEmitChunk);
-    const uint32_t r0 = chunk_rank[c];
-    // ranks overlapping [p0, p1): each has >= 1 pair, so at most kEmitChunk of them
-    const uint32_t r1 = (c + 1 < nchunks) ? chunk_rank[c + 1] : V - 1;
-    const uint32_t nr = min(r1 - r0 + 1, (uint32_t)kEmitChunk);
+  for (uint32_t c = blockIdx.x; c < nruns; c += gridDim.x) {
+    const uint32_t p0 = pbase + c * kEmitChunk;         // global pair indices [p0, p1)
+    const uint32_t p1 = pbase + min(P, (c + 1) * kEmitChunk);
     __syncthreads();
+    if (tid == 0) s_r0 = rank_of_pair(offsets, V, p0);
+    if (tid == 32) s_r1 = rank_of_pair(offsets, V, p1 - 1);
+    __syncthreads();
+    const uint32_t r0 = s_r0;
+    // ranks overlapping [p0, p1): each has >= 1 pair, so at most kEmitChunk of them
+    const uint32_t nr = min(s_r1 - r0 + 1, (uint32_t)kEmitChunk);
     for (uint32_t i = tid; i < nr; i += kBinThreads) {
       s_off[i] = offsets[r0 + i];
       s_box[i] = boxes[r0 + i];
@@ -209,8 +258,8 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
       const SplatRec& R = rec_sorted[r0 + lo];
       const bool hit = block_may_hit(R.a, R.b, (float)(bx * kBlock) + 0.5f, (float)(by * kBlock) + 0.5f);
       const uint32_t key = hit ? by * (uint32_t)gw + bx : kNone;
-      pair_keys[p] = key;
-      pair_vals[p] = r0 + lo;
+      pair_keys[p - pbase] = key;
+      pair_vals[p - pbase] = r0 + lo;
       if (hit) {
         ++live;
         for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
@@ -228,7 +277,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
 }
 
 // Block ranges [start, end) in the live pairs sorted by block id.  ranges must
-// be zero beforehand (the projection kernel clears them).
+// be zero beforehand (the chunk setup clears them).
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys,
                                                      const Header* __restrict__ hdr,
                                                      uint2* __restrict__ ranges, uint32_t nblocks) {
@@ -302,25 +351,35 @@ cudaError_t launch_block_order(const uint2* ranges, int nblocks, uint32_t split,
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const uint32_t* sorted_ids, const SplatRec* rec, const uint2* boxes_by_id,
-                       SplatRec* rec_sorted, float* g2d, Header* hdr,
-                       unsigned long long* scan_status, const uint32_t* epoch, uint32_t* offsets,
-                       uint2* boxes, uint32_t* chunk_rank, uint32_t* pair_keys,
-                       uint32_t* pair_vals, uint32_t pair_cap, int gw, int gh, int pair_passes,
-                       int n_cap, int grid_cap, cudaStream_t st) {
+cudaError_t launch_bin_count(const uint32_t* sorted_ids, const SplatRec* rec,
+                             const uint2* boxes_by_id, SplatRec* rec_sorted, float* g2d,
+                             Header* hdr, unsigned long long* scan_status, const uint32_t* epoch,
+                             uint32_t* offsets, uint2* boxes, uint32_t pair_cap, int chunked,
+                             int n_cap, int grid_cap, cudaStream_t st) {
   int tiles = (n_cap + kBinTile - 1) / kBinTile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > grid_cap) tiles = grid_cap;
   bin_count_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, boxes_by_id, rec_sorted,
                                                   reinterpret_cast<float4*>(g2d), hdr, scan_status,
-                                                  epoch, offsets, boxes, chunk_rank, pair_cap);
+                                                  epoch, offsets, boxes, pair_cap, chunked);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_chunk(const uint32_t* offsets, const uint2* boxes,
+                             const SplatRec* rec_sorted, Header* hdr, uint32_t* epoch, uint32_t k,
+                             uint32_t B,
+                             uint32_t pair_cap, int chunked, uint2* ranges, uint32_t* pair_keys,
+                             uint32_t* pair_vals, int gw, int gh, int pair_passes, int grid_cap,
+                             cudaStream_t st) {
+  chunk_setup_kernel<<<1, 256, 0, st>>>(offsets, hdr, epoch, k, B, pair_cap, chunked, ranges,
+                                        gw * gh);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int chunks = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
-  if (chunks > grid_cap) chunks = grid_cap;
-  if (chunks < 1) chunks = 1;
-  bin_emit_kernel<<<chunks, kBinThreads, 0, st>>>(offsets, boxes, chunk_rank, rec_sorted, hdr,
-                                                  pair_keys, pair_vals, gw, gh, pair_passes);
+  int runs = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
+  if (runs > grid_cap) runs = grid_cap;
+  if (runs < 1) runs = 1;
+  bin_emit_kernel<<<runs, kBinThreads, 0, st>>>(offsets, boxes, rec_sorted, hdr, pair_keys,
+                                                pair_vals, gw, gh, pair_passes);
   return cudaGetLastError();
 }
 
@@ -331,6 +390,5 @@ cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges
 }
 
 size_t bin_tiles(size_t n) { return (n + kBinTile - 1) / kBinTile; }
-size_t emit_chunks(size_t pairs) { return (pairs + kEmitChunk - 1) / kEmitChunk; }
 
 }  // namespace gsr

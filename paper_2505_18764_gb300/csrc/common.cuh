@@ -33,7 +33,8 @@ struct Header {
   uint32_t pairs;          // P (clamped to the capacity)
   uint32_t pairs_wanted;   // P before clamping
   uint32_t live_pairs;     // pairs whose block the ellipse reaches (the rest are dropped)
-  uint32_t pad0[3];
+  uint32_t pair_base;      // first (global) pair index of the current chunk
+  uint32_t pad0[2];
   uint32_t tile_counter[16];  // dynamic tile ids: [0..3] depth-sort passes, [4..7] pair passes,
                               // [8] bin scan, [9..] standalone sort
   uint32_t depth_hist[4][256];

@@ -161,12 +161,25 @@ __device__ __forceinline__ void write_fwd(const PixelFwd& p, int x, int y, int W
 }
 
 // One warp, one footprint COLS x 4 (two pixels per lane when COLS = 16).
+// resume: the pixel continues from the colour, transmittance, last rank and
+// count stored by the previous chunk (memory-efficiency mode).
+__device__ __forceinline__ void resume_fwd(PixelFwd& p, int x, int y, int W, int fmt,
+                                           const void* state, const uint32_t* last_out,
+                                           const uint32_t* ncontrib, float t_cull) {
+  const size_t pix = (size_t)y * W + x;
+  const float4 st = load_state(state, fmt, pix);
+  p.C0 = st.x; p.C1 = st.y; p.C2 = st.z; p.T = st.w;
+  p.last = last_out[pix];
+  p.n = ncontrib ? ncontrib[pix] : 0u;
+  p.done = p.T < t_cull;
+}
+
 template <int COLS>
 __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict__ rec,
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
                                          int x0, int y0, int lane, int W, int H, float t_cull,
                                          int fmt, float* image, void* state, uint32_t* last_out,
-                                         uint32_t* ncontrib) {
+                                         uint32_t* ncontrib, int resume) {
   constexpr int NPX = COLS == 16 ? 2 : 1;
   int x, ya;
   bool own;
@@ -176,6 +189,11 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
   PixelFwd pa{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(own && x < W && ya < H)};
   PixelFwd pb{1.f, 0.f, 0.f, 0.f, kNone, 0u, NPX == 1 || !(x < W && yb < H)};
+  if (resume) {
+    if (!pa.done) resume_fwd(pa, x, ya, W, fmt, state, last_out, ncontrib, t_cull);
+    if (!pb.done) resume_fwd(pb, x, yb, W, fmt, state, last_out, ncontrib, t_cull);
+  }
+  const bool wa = own && x < W && ya < H, wb = NPX == 2 && x < W && yb < H;
 
   const uint32_t beg = range.x, end = range.y;
   if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
@@ -216,8 +234,8 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
   }
   cp_async_wait_all();
   __syncwarp();
-  if (own) write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
-  if (NPX == 2) write_fwd(pb, x, yb, W, H, fmt, image, state, last_out, ncontrib);
+  if (wa) write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
+  if (wb) write_fwd(pb, x, yb, W, H, fmt, image, state, last_out, ncontrib);
 }
 
 __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const Header* __restrict__ hdr, uint32_t* __restrict__ next, uint32_t* __restrict__ item_cost,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, float* __restrict__ image, void* __restrict__ state,
-    uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib) {
+    uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib, int resume) {
   __shared__ WarpRing rings[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpRing& R = rings[warp];
@@ -237,13 +255,13 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const long long t0 = clock64();
     if (cols == 16)
       fwd_item<16>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
-                   last_out, ncontrib);
+                   last_out, ncontrib, resume);
     else if (cols == 8)
       fwd_item<8>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
-                  last_out, ncontrib);
+                  last_out, ncontrib, resume);
     else
       fwd_item<4>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
-                  last_out, ncontrib);
+                  last_out, ncontrib, resume);
     if (lane == 0) item_cost[idx] = (uint32_t)min(clock64() - t0, (long long)0xFFFFFFFF);
   }
 }
@@ -296,17 +314,25 @@ struct PixelBwd {
   uint32_t end;   // depth rank after the pixel's last fragment
 };
 
+// chunk_state (memory-efficiency mode): with chunk_in, (C', T) continue from the
+// previous chunk instead of (stored C, 1).
 __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, int y, int W,
                                                int fmt, const void* state,
-                                               const uint32_t* last_in, const float* dLdC) {
+                                               const uint32_t* last_in, const float* dLdC,
+                                               const float4* chunk_state, int chunk_in) {
   p.Cp0 = p.Cp1 = p.Cp2 = 0.f;
   p.g0 = p.g1 = p.g2 = 0.f;
   p.T = 1.f;
   p.end = 0;
   if (valid) {
     const size_t pix = (size_t)y * W + x;
-    const float4 st = load_state(state, fmt, pix);
-    p.Cp0 = st.x; p.Cp1 = st.y; p.Cp2 = st.z;
+    if (chunk_in) {
+      const float4 cs = chunk_state[pix];
+      p.Cp0 = cs.x; p.Cp1 = cs.y; p.Cp2 = cs.z; p.T = cs.w;
+    } else {
+      const float4 st = load_state(state, fmt, pix);
+      p.Cp0 = st.x; p.Cp1 = st.y; p.Cp2 = st.z;
+    }
     p.g0 = dLdC[3 * pix]; p.g1 = dLdC[3 * pix + 1]; p.g2 = dLdC[3 * pix + 2];
     const uint32_t l = last_in[pix];
     p.end = (l == kNone) ? 0u : l + 1u;
@@ -406,7 +432,8 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
                                          int x0, int y0, int lane, int W, int H, int fmt,
                                          const void* state, const uint32_t* last_in,
-                                         const float* dLdC, float* g2d, int threshold) {
+                                         const float* dLdC, float* g2d, int threshold,
+                                         float4* chunk_state, int chunk_in, int chunk_out) {
   constexpr int NPX = COLS == 16 ? 2 : 1;
   int x, ya;
   bool own;
@@ -416,9 +443,10 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
   const int tslot = transpose_slot(lane);
   PixelBwd pa, pb;
-  load_pixel_bwd(pa, own && x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
+  const bool va = own && x < W && ya < H, vb = NPX == 2 && x < W && yb < H;
+  load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
   if (NPX == 2) {
-    load_pixel_bwd(pb, x < W && yb < H, x, yb, W, fmt, state, last_in, dLdC);
+    load_pixel_bwd(pb, vb, x, yb, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
   } else {
     pb.Cp0 = pb.Cp1 = pb.Cp2 = 0.f;
     pb.g0 = pb.g1 = pb.g2 = 0.f;
@@ -469,6 +497,10 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
   }
   cp_async_wait_all();
   __syncwarp();
+  if (chunk_out) {
+    if (va) chunk_state[(size_t)ya * W + x] = make_float4(pa.Cp0, pa.Cp1, pa.Cp2, pa.T);
+    if (vb) chunk_state[(size_t)yb * W + x] = make_float4(pb.Cp0, pb.Cp1, pb.Cp2, pb.T);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -656,7 +688,8 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     const Header* __restrict__ hdr, uint32_t* __restrict__ next,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, const void* __restrict__ state, const uint32_t* __restrict__ last_in,
-    const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold, int back) {
+    const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold, int back,
+    float4* __restrict__ chunk_state, int chunk_in, int chunk_out) {
   __shared__ WarpRing rings[kWarps];
   __shared__ __align__(16) float s_part[kWarps][32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -686,13 +719,13 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     }
     if (cols == 16)
       bwd_item<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                         last_in, dLdC, g2d, threshold);
+                         last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
     else if (cols == 8)
       bwd_item<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                        last_in, dLdC, g2d, threshold);
+                        last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
     else
       bwd_item<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                        last_in, dLdC, g2d, threshold);
+                        last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
   }
 }
 
@@ -780,15 +813,16 @@ cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const 
                               uint32_t* next, uint32_t* item_cost, const uint32_t* pair_ranks,
                               const SplatRec* rec,
                               int W, int H, int gw, int gh, float t_cull, int fmt, float* image,
-                              void* state, uint32_t* last, uint32_t* ncontrib, int num_sms,
-                              cudaStream_t st) {
+                              void* state, uint32_t* last, uint32_t* ncontrib, int resume,
+                              int num_sms, cudaStream_t st) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   static const int per_sm = resident_per_sm(raster_fwd_kernel);
   const int grid = per_sm * num_sms;
   raster_fwd_kernel<<<grid, kThreads, 0, st>>>(ranges, items, hdr, next, item_cost, pair_ranks, rec,
-                                               W, H, gw, t_cull, fmt, image, state, last, ncontrib);
+                                               W, H, gw, t_cull, fmt, image, state, last, ncontrib,
+                                               resume);
   return cudaGetLastError();
 }
 
@@ -797,8 +831,8 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
                               uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
                               int W, int H, int gw, int gh, float t_cull, int fmt,
                               const void* state, const uint32_t* last, const float* dLdC,
-                              float* g2d, int mode, int threshold, int back, int num_sms,
-                              cudaStream_t st) {
+                              float* g2d, int mode, int threshold, int back, float4* chunk_state,
+                              int chunk_in, int chunk_out, int num_sms, cudaStream_t st) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
@@ -810,13 +844,13 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_NAIVE><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold, back);
+        threshold, back, chunk_state, chunk_in, chunk_out);
   } else {
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_WARP>);
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_WARP><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold, back);
+        threshold, back, chunk_state, chunk_in, chunk_out);
   }
   return cudaGetLastError();
 }

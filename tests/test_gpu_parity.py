@@ -543,3 +543,105 @@ def test_back_to_front_needs_a_precise_final_transmittance():
         err[order] = worst
     print(f"unorm8 state, worst gradient rel-L2: {err}")
     assert err["back_to_front"] > 2.0 * err["front_to_back"]
+
+
+# ---------------------------------------------------------------------------
+# Memory-efficiency mode: the view in chunks of the depth order
+# ---------------------------------------------------------------------------
+
+def _chunked_cases():
+    tiny, cam_t, _ = syn.tiny_scene_1k()
+    small, cam_s = _split_scenes()[0]
+    return [(tiny, cam_t, 2 * 64 + 40), (small, cam_s, 2 * 70 + 300)]
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_chunked_mode_matches_the_single_pass(which):
+    scene_np, cam, cap = _chunked_cases()[which]
+    g = syn.uniform_image(cam.height, cam.width, seed=83 + which, lo=-1.0, hi=1.0)
+    base = dict(sh_degree=scene_np.sh_degree)
+    s1, ws1, out1, gr1 = run_forward_backward(scene_np, cam, gs.RasterOpts(**base), g)
+    total = gs.read_counters(ws1)["pairs_wanted"]
+    oc = gs.RasterOpts(chunked=True, pair_capacity=cap, **base)
+    s2, ws2, out2, gr2 = run_forward_backward(scene_np, cam, oc, g)
+    assert ws2.c.n_chunks >= 3 and total > cap, (ws2.c.n_chunks, total, cap)
+    # FP32 state round trips are exact: the same image, state, last ranks and counts
+    for key in ("image", "state", "last", "n_contrib"):
+        assert torch.equal(out1[key], out2[key]), key
+    for k in GROUPS:
+        assert rel_l2(gr2[k], gr1[k]) < 1e-5, k
+    _check_backward(scene_np, cam, oc, g)
+
+
+def test_chunked_mode_reduced_precision_state():
+    """fp16 state rounds (C, T) at every chunk boundary, like the paper's
+    render-target round trips; still within the reduced-state bounds."""
+    scene_np, cam, cap = _chunked_cases()[0]
+    g = syn.uniform_image(cam.height, cam.width, seed=88, lo=-1.0, hi=1.0)
+    opts = gs.RasterOpts(state_format="fp16", chunked=True, pair_capacity=cap)
+    scene, ws, out, grads = run_forward_backward(scene_np, cam, opts, g)
+    ref_img = oracle.render(scene_np, cam, oracle_opts(opts, cam))
+    ok = (ref_img["ambig"] & AMBIG_IMAGE) == 0
+    img = out["image"].cpu().numpy().astype(np.float64)
+    assert np.abs(img - ref_img["color"]).max(axis=2)[ok].max() <= 2e-3
+    _check_backward(scene_np, cam, opts, g, tol=1e-2)
+
+
+def test_chunked_mode_rejections():
+    scene_np, cam, _ = syn.tiny_scene_1k()
+    scene = gs.SceneTensors.from_numpy(scene_np)
+    with pytest.raises(gs.GsError):   # capacity below twice the 64 blocks
+        o = gs.RasterOpts(chunked=True, pair_capacity=100)
+        ws = gs.Workspace(scene.n, cam.width, cam.height, o)
+        gs.render(ws, scene, cam, o)
+    o = gs.RasterOpts(chunked=True, pair_capacity=200)
+    ws = gs.Workspace(scene.n, cam.width, cam.height, o)
+    gs.project(ws, scene, cam, o)
+    gs.sort(ws)
+    with pytest.raises(gs.GsError):   # the split entry points do not chunk
+        gs.bin(ws, cam, o)
+    with pytest.raises(gs.GsError):   # chunks are walked front to back only
+        gs.Workspace(scene.n, cam.width, cam.height,
+                     gs.RasterOpts(chunked=True, pair_capacity=200, backward_order="back_to_front"))
+
+
+def test_chunked_mode_with_multi_tile_chunks():
+    """Chunks of several pair-sort tiles (2048 pairs each), so the sort's
+    look-back runs inside every chunk of the forward and again in the backward."""
+    scene_np = syn.cube_scene(40000, seed=89, sh_degree=1, log_scale_mean=-4.0, log_scale_std=0.5)
+    cam = syn.look_at((0.0, 0.0, -2.8), (0.0, 0.0, 0.0), 55.0, 256, 256)
+    g = syn.uniform_image(cam.height, cam.width, seed=90, lo=-1.0, hi=1.0)
+    s1, ws1, out1, gr1 = run_forward_backward(scene_np, cam, gs.RasterOpts(sh_degree=1), g)
+    total = gs.read_counters(ws1)["pairs_wanted"]
+    cap = 7000
+    assert total > 4 * cap, total
+    oc = gs.RasterOpts(sh_degree=1, chunked=True, pair_capacity=cap)
+    s2, ws2, out2, gr2 = run_forward_backward(scene_np, cam, oc, g)
+    for key in ("image", "state", "last", "n_contrib"):
+        assert torch.equal(out1[key], out2[key]), key
+    for k in GROUPS:
+        assert rel_l2(gr2[k], gr1[k]) < 1e-5, k
+
+
+def test_sort_and_bin_repeat_for_one_projection():
+    """A second sort or binning of the same projection gives the same lists
+    (fresh tile counters and look-back tags each time)."""
+    scene_np = syn.cube_scene(40000, seed=91, sh_degree=0, log_scale_mean=-4.0)
+    cam = syn.look_at((0.0, 0.0, -2.8), (0.0, 0.0, 0.0), 55.0, 256, 256)
+    opts = gs.RasterOpts()
+    scene = gs.SceneTensors.from_numpy(scene_np)
+    ws = gs.Workspace(scene.n, cam.width, cam.height, opts)
+    gs.project(ws, scene, cam, opts)
+    lists = []
+    for rep in range(3):
+        gs.sort(ws)
+        gs.bin(ws, cam, opts)
+        c = gs.read_counters(ws)
+        lists.append((gs.copy_array(ws, gs._lib.GS_ARRAY_SORTED_IDS, c["visible"]).cpu(),
+                      gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_BLOCKS, c["live_pairs"]).cpu(),
+                      gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_RANKS, c["live_pairs"]).cpu()))
+        gs.check_status(ws)
+    assert c["visible"] > 4096 and c["live_pairs"] > 4096
+    for l in lists[1:]:
+        for a, b in zip(lists[0], l):
+            assert torch.equal(a, b)
