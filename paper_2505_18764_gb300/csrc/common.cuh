@@ -81,6 +81,31 @@ __device__ __forceinline__ float frag_q(float px, float py, const float4& a, con
   return __fmaf_rn(y1, y1, __fmul_rn(y2, y2));
 }
 
+// frag_q for the two pixels (px, pya) and (px, pyb) of one column: dx and y1
+// are common, and each q is bit-identical to frag_q's.
+__device__ __forceinline__ void frag_q2(float px, float pya, float pyb, const float4& a,
+                                        const float4& b, float& y1, float& y2a, float& y2b,
+                                        float& qa, float& qb) {
+  const float dx = __fsub_rn(__fsub_rn(px, a.x), b.z);
+  const float dya = __fsub_rn(__fsub_rn(pya, a.y), b.w);
+  const float dyb = __fsub_rn(__fsub_rn(pyb, a.y), b.w);
+  y1 = __fmul_rn(a.z, dx);
+  y2a = __fmul_rn(b.x, __fmaf_rn(-a.w, dx, dya));
+  y2b = __fmul_rn(b.x, __fmaf_rn(-a.w, dx, dyb));
+  qa = __fmaf_rn(y1, y1, __fmul_rn(y2a, y2a));
+  qb = __fmaf_rn(y1, y1, __fmul_rn(y2b, y2b));
+}
+
+// frag_alpha for a fragment that may be absent: a miss gets G = 0, so alpha,
+// alpha T and every term derived from them are exact zeros and T * (1 - alpha)
+// leaves T unchanged.
+__device__ __forceinline__ float frag_alpha_masked(bool hit, float opacity, float q, float& G,
+                                                   float& at) {
+  G = hit ? ex2_approx(-q) : 0.0f;
+  at = __fmul_rn(opacity, G);
+  return fminf(kAlphaMax, at);
+}
+
 __device__ __forceinline__ float frag_alpha(float opacity, float q, float& G, float& at) {
   G = ex2_approx(-q);
   at = __fmul_rn(opacity, G);

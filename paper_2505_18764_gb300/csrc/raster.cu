@@ -133,15 +133,17 @@ struct PixelFwd {
   bool done;
 };
 
-__device__ __forceinline__ void blend(PixelFwd& p, float alpha, const float4& c, uint32_t rank,
-                                      float t_cull) {
+// One fragment (hit false would make it an exact no-op: alpha = 0 leaves C and
+// T unchanged).
+__device__ __forceinline__ void blend(PixelFwd& p, bool hit, float alpha, const float4& c,
+                                      uint32_t rank, float t_cull) {
   const float w = __fmul_rn(alpha, p.T);
   p.C0 = __fmaf_rn(w, c.x, p.C0);
   p.C1 = __fmaf_rn(w, c.y, p.C1);
   p.C2 = __fmaf_rn(w, c.z, p.C2);
   p.T = next_T(p.T, alpha);
-  p.last = rank;
-  ++p.n;
+  p.last = hit ? rank : p.last;
+  p.n += hit ? 1u : 0u;
   if (p.T < t_cull) p.done = true;   // every later fragment is T-culled
 }
 
@@ -213,21 +215,19 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
       m &= m - 1u;
       const float4 a = R.a[slot][j];
       const float4 b = R.b[slot][j];
-      float y1, y2;
-      const float qa = frag_q(px, pya, a, b, y1, y2);
+      float y1, y2a, y2b = 0.f, qa, qb = 0.f;
+      if (NPX == 2)
+        frag_q2(px, pya, pyb, a, b, y1, y2a, y2b, qa, qb);
+      else
+        qa = frag_q(px, pya, a, b, y1, y2a);
       const bool ha = !pa.done && qa <= b.y;   // alpha >= 1/255
-      float qb = 0.f;
-      bool hb = false;
-      if (NPX == 2) {
-        qb = frag_q(px, pyb, a, b, y1, y2);
-        hb = !pb.done && qb <= b.y;
-      }
+      const bool hb = NPX == 2 && !pb.done && qb <= b.y;
       if (!(ha || hb)) continue;
       const float4 c = R.c[slot][j];
       const uint32_t rank = R.rank[slot][j];
       float G, at;
-      if (ha) blend(pa, frag_alpha(c.w, qa, G, at), c, rank, t_cull);
-      if (NPX == 2 && hb) blend(pb, frag_alpha(c.w, qb, G, at), c, rank, t_cull);
+      if (ha) blend(pa, true, frag_alpha(c.w, qa, G, at), c, rank, t_cull);
+      if (NPX == 2 && hb) blend(pb, true, frag_alpha(c.w, qb, G, at), c, rank, t_cull);
     }
     __syncwarp();   // every lane is done with the slot before it is refilled
     ring_issue(R, slot, rec, ip, end, rk_next, lane);
@@ -344,17 +344,23 @@ __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, i
 // below its end rank: the forward stopped after the fragment that took T
 // under t_cull, and the same arithmetic in the same order gives the same T
 // here, so Procedure 1's cull test needs no second evaluation.
-__device__ __forceinline__ void grad_fragment(PixelBwd& p, float q, float y1, float y2,
+//
+// A missed pixel (hit false) runs the same code with G = 0: every term is an
+// exact zero and the state is unchanged, so a warp handles both of a lane's
+// pixels without branching.  FIRST writes v instead of adding to it.
+template <bool FIRST>
+__device__ __forceinline__ void grad_fragment(PixelBwd& p, bool hit, float q, float y1, float y2,
                                               const float4& a, const float4& b, const float4& c,
                                               float v[9]) {
   float G, at;
-  const float alpha = frag_alpha(c.w, q, G, at);
+  const float alpha = frag_alpha_masked(hit, c.w, q, G, at);
   const float oma = __fsub_rn(1.0f, alpha);
   const float wT = __fmul_rn(alpha, p.T);
+  float t[9];
   // Eq. 3
-  v[5] += p.g0 * wT;
-  v[6] += p.g1 * wT;
-  v[7] += p.g2 * wT;
+  t[5] = p.g0 * wT;
+  t[6] = p.g1 * wT;
+  t[7] = p.g2 * wT;
   // Eq. 7 with C'_i before its update
   const float dLda = (p.g0 * (c.x * p.T - p.Cp0) + p.g1 * (c.y * p.T - p.Cp1) +
                       p.g2 * (c.z * p.T - p.Cp2)) * __fdividef(1.0f, oma);
@@ -365,18 +371,20 @@ __device__ __forceinline__ void grad_fragment(PixelBwd& p, float q, float y1, fl
   p.T = next_T(p.T, alpha);
   // alpha = min(0.99, o G): no gradient through the clamp
   const float d_at = at < kAlphaMax ? dLda : 0.f;
-  v[8] += G * d_at;
+  t[8] = G * d_at;
   // z = Sigma^-1 d = L^-T L^-1 d, in units of 1 / (2 ln 2):
   // dpower/dmu_2D = z and dpower/dSigma_2D = z z^T / 2
   const float w = at * d_at;
   const float z1 = b.x * y2;
   const float z0 = a.z * y1 - a.w * z1;
   const float wz0 = w * z0, wz1 = w * z1;
-  v[0] += wz0;
-  v[1] += wz1;
-  v[2] += wz0 * z0;
-  v[3] += wz0 * z1;
-  v[4] += wz1 * z1;
+  t[0] = wz0;
+  t[1] = wz1;
+  t[2] = wz0 * z0;
+  t[3] = wz0 * z1;
+  t[4] = wz1 * z1;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = FIRST ? t[k] : v[k] + t[k];
 }
 
 __device__ __forceinline__ void red_add9(float* dst, const float v[9]) {
@@ -474,21 +482,20 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
       const int j = __ffs(m) - 1;
       m &= m - 1u;
       const uint32_t rank = R.rank[slot][j];
-      float v[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) v[q] = 0.f;
       const float4 a = R.a[slot][j];
       const float4 b = R.b[slot][j];
-      float y1a, y2a, y1b = 0.f, y2b = 0.f, qb = 0.f;
-      const float qa = frag_q(px, pya, a, b, y1a, y2a);
-      if (NPX == 2) qb = frag_q(px, pyb, a, b, y1b, y2b);
+      float y1, y2a, y2b = 0.f, qa, qb = 0.f;
+      if (NPX == 2)
+        frag_q2(px, pya, pyb, a, b, y1, y2a, y2b, qa, qb);
+      else
+        qa = frag_q(px, pya, a, b, y1, y2a);
       const bool ha = rank < pa.end && qa <= b.y;
       const bool hb = NPX == 2 && rank < pb.end && qb <= b.y;
-      if (ha || hb) {
-        const float4 c = R.c[slot][j];
-        if (ha) grad_fragment(pa, qa, y1a, y2a, a, b, c, v);
-        if (NPX == 2 && hb) grad_fragment(pb, qb, y1b, y2b, a, b, c, v);
-      }
+      if (!__any_sync(kFull, ha || hb)) continue;
+      const float4 c = R.c[slot][j];
+      float v[9];
+      grad_fragment<true>(pa, ha, qa, y1, y2a, a, b, c, v);
+      if (NPX == 2) grad_fragment<false>(pb, hb, qb, y1, y2b, a, b, c, v);
       reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
     }
     flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
