@@ -319,11 +319,17 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restri
                                                           Header* __restrict__ hdr) {
   __shared__ uint32_t s_cnt[kOrderBuckets];
   __shared__ uint32_t s_pos[kOrderBuckets];
+  const int lane = threadIdx.x & 31;
+  const int nb_pad = (nblocks + 31) & ~31;
   for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const uint32_t len = ranges[b].y - ranges[b].x;
-    atomicAdd(&s_cnt[length_bucket(len)], block_items(len, split));
+  // lanes with the same bucket and item count add together
+  for (int b = threadIdx.x; b < nb_pad; b += blockDim.x) {
+    const uint32_t len = b < nblocks ? ranges[b].y - ranges[b].x : 0u;
+    const int bkt = b < nblocks ? length_bucket(len) : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, bkt * 32 + (int)block_items(len, split));
+    if (bkt >= 0 && lane == __ffs(peers) - 1)
+      atomicAdd(&s_cnt[bkt], block_items(len, split) * (uint32_t)__popc(peers));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -335,11 +341,17 @@ __global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restri
     hdr->n_items = run;
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const uint32_t len = ranges[b].y - ranges[b].x;
+  for (int b = threadIdx.x; b < nb_pad; b += blockDim.x) {
+    const uint32_t len = b < nblocks ? ranges[b].y - ranges[b].x : 0u;
+    const int bkt = b < nblocks ? length_bucket(len) : -1;
     const uint32_t n = block_items(len, split);
+    const uint32_t peers = __match_any_sync(0xffffffffu, bkt * 32 + (int)n);
+    const int leader = __ffs(peers) - 1;
+    uint32_t pos = 0;
+    if (bkt >= 0 && lane == leader) pos = atomicAdd(&s_pos[bkt], n * (uint32_t)__popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + n * (uint32_t)__popc(peers & lanemask_lt());
+    if (bkt < 0) continue;
     const uint32_t code0 = n == 16u ? 16u : (n == 8u ? 8u : 0u);
-    const uint32_t pos = atomicAdd(&s_pos[length_bucket(len)], n);
     for (uint32_t k = 0; k < n; ++k) items[pos + k] = ((uint32_t)b << 5) | (code0 + k);
   }
 }

@@ -754,9 +754,16 @@ __global__ void __launch_bounds__(1024) item_order_kernel(const uint32_t* __rest
                                                          uint32_t* __restrict__ out) {
   __shared__ uint32_t s_cnt[kCostBuckets];
   const uint32_t n = hdr->n_items;
+  const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kCostBuckets; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[cost_bucket(cost[i])], 1u);
+  // lanes with the same bucket add together (most items share a few buckets)
+  const uint32_t n_pad = (n + 31u) & ~31u;
+  for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+    const int bkt = i < n ? cost_bucket(cost[i]) : -1;
+    const uint32_t peers = __match_any_sync(kFull, bkt);
+    if (bkt >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[bkt], (uint32_t)__popc(peers));
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -767,8 +774,15 @@ __global__ void __launch_bounds__(1024) item_order_kernel(const uint32_t* __rest
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-    out[atomicAdd(&s_cnt[cost_bucket(cost[i])], 1u)] = items[i];
+  for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+    const int bkt = i < n ? cost_bucket(cost[i]) : -1;
+    const uint32_t peers = __match_any_sync(kFull, bkt);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (bkt >= 0 && lane == leader) base = atomicAdd(&s_cnt[bkt], (uint32_t)__popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (bkt >= 0) out[base + __popc(peers & lanemask_lt())] = items[i];
+  }
 }
 
 // ---------------------------------------------------------------------------
