@@ -266,6 +266,13 @@ const char* gs_last_error(void);
  * ellipse reaches: the sorted pair arrays hold these).  out holds 6. */
 int gs_read_counters(gs_workspace* ws, int64_t* out, gs_stream_t stream);
 
+/* Measurement helper, not part of the paper's method: the FP32 FMA rate of the
+ * current GPU in TFLOP/s (the ceiling of the FP32-bound raster kernels), from
+ * one launch of `iters` rounds of independent FMAs on every resident thread,
+ * timed with CUDA events on `stream`.  Synchronises `stream`; writes *tflops
+ * (host). */
+int gs_fp32_fma_rate(int32_t iters, double* tflops, gs_stream_t stream);
+
 /* Copies an internal array of `ws` into caller device memory `dst` (`bytes`):
  * GS_ARRAY_SORTED_IDS u32 [V], GS_ARRAY_DEPTH_KEYS u32 [n] (0xFFFFFFFF = culled),
  * GS_ARRAY_RECORDS float [n][12] (mu_x, mu_y, i11, k, i22, tau, mu_x_lo, mu_y_lo,

@@ -75,6 +75,11 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
+def set_threads(n: int) -> int:
+    """Threads the oracle's parallel loops use (0: all cores); returns the count."""
+    return int(_load().oracle_set_threads(ctypes.c_int(int(n))))
+
+
 def sh_basis(deg: int, dirs: np.ndarray, grad: bool = False):
     dirs = _d(dirs).reshape(-1, 3)
     n = dirs.shape[0]

@@ -595,6 +595,14 @@ extern "C" {
 
 int oracle_num_threads() { return num_threads(); }
 
+// Threads the parallel loops use from now on (0 or less: all cores).
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#endif
+  return num_threads();
+}
+
 // Y[n][K] (and dY[n][K][3] if non-null) for unit directions dirs[n][3].
 int oracle_sh_basis(int deg, const double* dirs, int n, double* Y, double* dY) {
   if (deg < 0 || deg > 3) return -1;

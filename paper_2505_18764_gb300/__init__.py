@@ -330,6 +330,14 @@ def render(ws: Workspace, scene: SceneTensors, cam, opts: RasterOpts, stream=Non
     return raster_forward(ws, cam, opts, stream=stream, **kw)
 
 
+def fp32_fma_rate(iters: int = 1 << 16, stream=None) -> float:
+    """Measured FP32 FMA rate of the current GPU in TFLOP/s (a measurement helper)."""
+    out = ctypes.c_double(0.0)
+    check(_lib.load().gs_fp32_fma_rate(int(iters), ctypes.byref(out), _stream(stream)),
+          "gs_fp32_fma_rate")
+    return float(out.value)
+
+
 def check_status(ws: Workspace, stream=None):
     check(_lib.load().gs_check_status(ws.ref, _stream(stream)), "gs_check_status")
 
@@ -441,5 +449,5 @@ def render_batch(requests, ws: Workspace, stream=None):
 __all__ = ["RasterOpts", "SceneTensors", "Workspace", "project", "sort", "raster_forward", "bin",
            "blend_forward", "blend_backward", "project_backward",
            "raster_backward", "loss", "render", "render_batch", "Request", "check_status",
-           "read_counters", "copy_array", "sort_pairs", "sort_pairs_noalloc", "decode_state", "alloc_state",
+           "read_counters", "fp32_fma_rate", "copy_array", "sort_pairs", "sort_pairs_noalloc", "decode_state", "alloc_state",
            "camera_to_c", "GsError", "zero_grads", "NONE_RANK"]
