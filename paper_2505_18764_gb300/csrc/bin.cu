@@ -181,7 +181,6 @@ __global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __rest
                                                           uint32_t B, uint32_t pair_cap,
                                                           int chunked, uint2* __restrict__ ranges,
                                                           int nblocks) {
-  __shared__ uint32_t s_lo, s_hi;
   const uint32_t V = hdr->visible, total = hdr->pairs_wanted;
   if (threadIdx.x == 0) {
     uint32_t lo = 0, hi = min(total, pair_cap);
@@ -199,8 +198,6 @@ __global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __rest
       lo = first_at((unsigned long long)k * B);
       hi = first_at((unsigned long long)(k + 1) * B);
     }
-    s_lo = lo;
-    s_hi = hi;
     *epoch += 1u;
     hdr->pair_base = lo;
     hdr->pairs = hi - lo;

@@ -312,79 +312,184 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_fwd_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Backward projection: one thread per visible depth rank.
-// g2 (12 floats per rank): the raster's sums over fragments of w z_hat and
-// w z_hat z_hat^T (z_hat = Sigma_2D^-1 d / (2 ln 2), w = alpha_tilde dL/dalpha_tilde),
-// then dL/d(rgb) and dL/do; converted here to dL/dmu_2D and dL/dSigma_2D.
+// Backward projection: the chain rule from the raster's per-splat sums to the
+// splat parameters.  g2d holds 12 floats per depth rank: the sums over the
+// splat's fragments of w z_hat and w z_hat z_hat^T (z_hat = Sigma_2D^-1 d in
+// units of 1 / (2 ln 2), w = alpha dL/dalpha), then dL/d(rgb) and dL/do;
+// they are converted here to dL/dmu_2D and dL/dSigma_2D.
+//
+// Only the splats that some fragment gave a gradient need the chain rule,
+// and they are a fraction of the depth-ranked list.  As in the forward pass,
+// each warp first reads the sums of 32 consecutive ranks, queues the ranks
+// with a non-zero sum in shared memory, and handles 32 queued splats at a
+// time with all lanes busy.
+//
+// The splats of a batch sit at scattered ids, so one lane per splat reading
+// its own rows would make every memory instruction touch 32 cache lines.
+// Instead the warp moves the rows between global and shared memory together:
+// consecutive lanes take consecutive words of the batch's rows (a mean is 3
+// floats, an SH row 3 (DEG+1)^2), so an instruction touches about 32 / (row
+// length) lines.  Each lane then computes from its row in shared memory and
+// leaves its gradients there, and the warp adds them to the gradient arrays
+// the same way (every id occurs once, so the read-modify-writes do not race).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void project_bwd_one(
-    const float* __restrict__ means, const float* __restrict__ scales,
-    const float4* __restrict__ quats, const float* __restrict__ opac,
-    const float* __restrict__ sh, int deg, const CamDev& cam, int clamp01,
-    const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ g2d, uint32_t r,
-    float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_opac, float* __restrict__ d_sh) {
-  const float4 ga = g2d[3 * r], gb = g2d[3 * r + 1], gc = g2d[3 * r + 2];
-  if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
-      gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
-    return;  // no fragment of this splat received a gradient
-  const uint32_t id = sorted_ids[r];
-  const float mx = means[3 * id], my = means[3 * id + 1], mz = means[3 * id + 2];
-  const float sx = scales[3 * id], sy = scales[3 * id + 1], sz = scales[3 * id + 2];
+constexpr int kProjBwdThreads = 128;
+constexpr int kProjBwdWarps = kProjBwdThreads / 32;
+
+// One splat's row in shared memory (floats): [0, 3) mean, then dL/dmean;
+// [3, 6) scale, then dL/dscale; [8, 8 + kSh) SH coefficients, then dL/dsh.
+// The pitch is an odd number of 16-byte words, so 32 lanes reading float4s of
+// their own rows hit distinct banks.
+template <int DEG>
+struct BwdRow {
+  static constexpr int kSh = 3 * (DEG + 1) * (DEG + 1);
+  static constexpr int kShOff = 8;
+  static constexpr int kRound = (kShOff + kSh + 3) / 4 * 4;
+  static constexpr int kPitch = (kRound / 4) % 2 == 1 ? kRound : kRound + 4;
+  static constexpr bool kVec = kSh % 4 == 0;
+};
+
+// gd += sum_k w_k dY_k / d(x, y, z) for the polynomials of sh_eval, with no
+// per-coefficient array (every term is used once).
+template <int DEG>
+__device__ __forceinline__ void sh_grad_dot(float x, float y, float z, const float* w, float* gd) {
+  if (DEG < 1) return;
+  gd[0] -= ShConst::c1 * w[3];
+  gd[1] -= ShConst::c1 * w[1];
+  gd[2] += ShConst::c1 * w[2];
+  if (DEG < 2) return;
+  gd[0] += ShConst::c2a * (y * w[4] - z * w[7]) + 2.0f * ShConst::c2c * x * w[8];
+  gd[1] += ShConst::c2a * (x * w[4] - z * w[5]) - 2.0f * ShConst::c2c * y * w[8];
+  gd[2] += 6.0f * ShConst::c2b * z * w[6] - ShConst::c2a * (y * w[5] + x * w[7]);
+  if (DEG < 3) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  const float a = 3.0f * xx - 3.0f * yy, b = 5.0f * zz - 1.0f;
+  gd[0] += -ShConst::c3a * (6.0f * x * y * w[9] + a * w[15]) + ShConst::c3b * y * z * w[10] -
+           ShConst::c3c * b * w[13] + 2.0f * ShConst::c3e * x * z * w[14];
+  gd[1] += ShConst::c3a * (6.0f * x * y * w[15] - a * w[9]) + ShConst::c3b * x * z * w[10] -
+           ShConst::c3c * b * w[11] - 2.0f * ShConst::c3e * y * z * w[14];
+  gd[2] += ShConst::c3b * x * y * w[10] - 10.0f * ShConst::c3c * z * (y * w[11] + x * w[13]) +
+           ShConst::c3d * (15.0f * zz - 3.0f) * w[12] + ShConst::c3e * (xx - yy) * w[14];
+}
+
+// The warp's rows of `len` floats at src[id_j * len] (j < count; id_j in lane
+// j's `id`) into rows[j * pitch + off], consecutive lanes on consecutive words.
+template <int LEN, int PITCH>
+__device__ __forceinline__ void gather_rows(float* rows, int off, const float* __restrict__ src,
+                                            uint32_t id, int count, int lane) {
+#pragma unroll 4
+  for (int t = 0; t < LEN; ++t) {
+    const int i = t * 32 + lane, j = i / LEN, c = i % LEN;
+    const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+    if (j < count) rows[j * PITCH + off + c] = src[(size_t)idj * LEN + c];
+  }
+}
+
+// dst[id_j * len + c] += rows[j * pitch + off + c], laid out as gather_rows.
+template <int LEN, int PITCH>
+__device__ __forceinline__ void scatter_add_rows(const float* rows, int off,
+                                                 float* __restrict__ dst, uint32_t id, int count,
+                                                 int lane) {
+#pragma unroll 4
+  for (int t = 0; t < LEN; ++t) {
+    const int i = t * 32 + lane, j = i / LEN, c = i % LEN;
+    const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+    if (j < count) dst[(size_t)idj * LEN + c] += rows[j * PITCH + off + c];
+  }
+}
+
+// As the two above for rows of LEN4 16-byte words (both sides 16-byte aligned).
+template <int LEN4, int PITCH>
+__device__ __forceinline__ void gather_rows4(float* rows, int off, const float* __restrict__ src,
+                                             uint32_t id, int count, int lane) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll 4
+  for (int t = 0; t < LEN4; ++t) {
+    const int i = t * 32 + lane, j = i / LEN4, c = i % LEN4;
+    const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+    if (j < count)
+      *reinterpret_cast<float4*>(rows + j * PITCH + off + 4 * c) = s4[(size_t)idj * LEN4 + c];
+  }
+}
+
+template <int LEN4, int PITCH>
+__device__ __forceinline__ void scatter_add_rows4(const float* rows, int off,
+                                                  float* __restrict__ dst, uint32_t id, int count,
+                                                  int lane) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll 4
+  for (int t = 0; t < LEN4; ++t) {
+    const int i = t * 32 + lane, j = i / LEN4, c = i % LEN4;
+    const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+    if (j < count) {
+      const float4 g = *reinterpret_cast<const float4*>(rows + j * PITCH + off + 4 * c);
+      float4 v = d4[(size_t)idj * LEN4 + c];
+      v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w;
+      d4[(size_t)idj * LEN4 + c] = v;
+    }
+  }
+}
+
+// The chain rule for one splat: its row (mean, scale, SH) in shared memory,
+// its quaternion and its 2D sums given.  dL/dmean, dL/dscale and dL/dsh go
+// back into the row; dL/dq is returned.
+template <int DEG>
+__device__ __forceinline__ float4 project_bwd_splat(float* row, const float4 quat, const float4 ga,
+                                                    const float4 gb, const CamDev& cam,
+                                                    int clamp01) {
+  using Row = BwdRow<DEG>;
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const float mx = row[0], my = row[1], mz = row[2];
+  const float sx = row[3], sy = row[4], sz = row[5];
   ProjState ps;
-  project_core(cam, mx, my, mz, quats[id], sx, sy, sz, ps);
+  project_core(cam, mx, my, mz, quat, sx, sy, sz, ps);
   // 2D gradients in natural units: dL/dmu_2D = 2 ln2 (v0, v1) and
-  // dL/dSigma_2D = 2 ln2^2 [[v2, v3], [v3, v4]] (the raster accumulated
-  // z = Sigma^-1 d in units of 1 / (2 ln 2))
+  // dL/dSigma_2D = 2 ln2^2 [[v2, v3], [v3, v4]]
   const float gmu2x = 2.f * kLn2 * ga.x, gmu2y = 2.f * kLn2 * ga.y;
   const float gs_scale = 2.f * kLn2 * kLn2;
   const float GS00 = gs_scale * ga.z, GS01 = gs_scale * ga.w, GS11 = gs_scale * gb.x;
-  const float grgb[3] = {gb.y, gb.z, gb.w};
-  const float gop = gc.x;
   float gmu[3] = {0.f, 0.f, 0.f};
 
-  // colour: rgb = clamp(sum sh Y + 0.5)
+  // colour: rgb = clamp(sum_k sh_k Y_k(d) + 0.5), d = (mu - campos) / |mu - campos|
   {
-    const int K = (deg + 1) * (deg + 1);
-    float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+    const float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
     const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
     const float dx = vx * rn, dy = vy * rn, dz = vz * rn;
     float Y[16];
-    sh_eval(deg, dx, dy, dz, Y);
-    const float* shp = sh + (size_t)id * K * 3;
+    sh_eval(DEG, dx, dy, dz, Y);
+    float* shr = row + Row::kShOff;
     float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
     for (int k = 0; k < K; ++k) {
-      raw[0] += shp[k * 3 + 0] * Y[k];
-      raw[1] += shp[k * 3 + 1] * Y[k];
-      raw[2] += shp[k * 3 + 2] * Y[k];
+      raw[0] += shr[k * 3 + 0] * Y[k];
+      raw[1] += shr[k * 3 + 1] * Y[k];
+      raw[2] += shr[k * 3 + 2] * Y[k];
     }
+    const float grgb[3] = {gb.y, gb.z, gb.w};
     float graw[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const bool pass = raw[c] > 0.f && (!clamp01 || raw[c] < 1.f);
       graw[c] = pass ? grgb[c] : 0.f;
     }
-    float* dsh = d_sh + (size_t)id * K * 3;
-    for (int k = 0; k < K; ++k) {
-      dsh[k * 3 + 0] += Y[k] * graw[0];
-      dsh[k * 3 + 1] += Y[k] * graw[1];
-      dsh[k * 3 + 2] += Y[k] * graw[2];
-    }
-    if (deg > 0) {
-      float dY[48];
-      sh_grad(deg, dx, dy, dz, dY);
+    // read the coefficients again below rather than hold them in registers
+    asm volatile("" ::: "memory");
+    if (DEG > 0) {
+      // through the view direction: w_k = sh_k . graw, dL/dd = sum_k w_k dY_k/dd
+      float w[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        w[k] = shr[k * 3 + 0] * graw[0] + shr[k * 3 + 1] * graw[1] + shr[k * 3 + 2] * graw[2];
       float gd[3] = {0.f, 0.f, 0.f};
-      for (int k = 1; k < K; ++k) {
-        const float w = shp[k * 3 + 0] * graw[0] + shp[k * 3 + 1] * graw[1] + shp[k * 3 + 2] * graw[2];
-        gd[0] += w * dY[k * 3 + 0];
-        gd[1] += w * dY[k * 3 + 1];
-        gd[2] += w * dY[k * 3 + 2];
-      }
+      sh_grad_dot<DEG>(dx, dy, dz, w, gd);
       const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
       gmu[0] += (gd[0] - dx * dd) * rn;
       gmu[1] += (gd[1] - dy * dd) * rn;
       gmu[2] += (gd[2] - dz * dd) * rn;
     }
+    // dL/dsh_k = Y_k graw replaces the coefficients
+#pragma unroll
+    for (int i = 0; i < Row::kSh; ++i) shr[i] = Y[i / 3] * graw[i % 3];
   }
 
   // Sigma_2D = N N^T + 0.3 I:  G_N = 2 G_S N;  N = Tm M:  G_Tm = G_N M^T, G_M = Tm^T G_N
@@ -441,30 +546,113 @@ __device__ __forceinline__ void project_bwd_one(
   gq[3] = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] +
                  y * GR[5] + x * GR[6] + y * GR[7]);
   const float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
-  d_quats[4 * id + 0] += (gq[0] - w * qd) * ps.rq;
-  d_quats[4 * id + 1] += (gq[1] - x * qd) * ps.rq;
-  d_quats[4 * id + 2] += (gq[2] - y * qd) * ps.rq;
-  d_quats[4 * id + 3] += (gq[3] - z * qd) * ps.rq;
-  d_scales[3 * id + 0] += gs[0];
-  d_scales[3 * id + 1] += gs[1];
-  d_scales[3 * id + 2] += gs[2];
-  d_means[3 * id + 0] += gmu[0];
-  d_means[3 * id + 1] += gmu[1];
-  d_means[3 * id + 2] += gmu[2];
-  d_opac[id] += gop;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    row[j] = gmu[j];
+    row[3 + j] = gs[j];
+  }
+  return make_float4((gq[0] - w * qd) * ps.rq, (gq[1] - x * qd) * ps.rq,
+                     (gq[2] - y * qd) * ps.rq, (gq[3] - z * qd) * ps.rq);
 }
 
-__global__ void __launch_bounds__(128) project_bwd_kernel(
-    const float* __restrict__ means, const float* __restrict__ scales,
-    const float4* __restrict__ quats, const float* __restrict__ opac,
-    const float* __restrict__ sh, int deg, CamDev cam, int clamp01,
+// One batch of `count` (<= 32) queued ranks, lane j holding rank r.
+template <int DEG>
+__device__ __forceinline__ void project_bwd_batch(
+    float* rows, uint32_t r, int count, int lane, const float* __restrict__ means,
+    const float* __restrict__ scales, const float4* __restrict__ quats,
+    const float* __restrict__ sh, bool sh_vec, bool dq_vec, const CamDev& cam, int clamp01,
     const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ g2d,
-    const Header* __restrict__ hdr, float* __restrict__ d_means, float* __restrict__ d_scales,
-    float* __restrict__ d_quats, float* __restrict__ d_opac, float* __restrict__ d_sh) {
+    float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
+    float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  using Row = BwdRow<DEG>;
+  constexpr int P = Row::kPitch;
+  const bool mine = lane < count;
+  const uint32_t id = mine ? sorted_ids[r] : 0u;
+  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, quat = ga;
+  float gop = 0.f;
+  if (mine) {
+    ga = g2d[3 * r];
+    gb = g2d[3 * r + 1];
+    gop = reinterpret_cast<const float*>(g2d)[12 * r + 8];
+    quat = quats[id];
+  }
+  gather_rows<3, P>(rows, 0, means, id, count, lane);
+  gather_rows<3, P>(rows, 3, scales, id, count, lane);
+  if (Row::kVec && sh_vec)
+    gather_rows4<Row::kSh / 4, P>(rows, Row::kShOff, sh, id, count, lane);
+  else
+    gather_rows<Row::kSh, P>(rows, Row::kShOff, sh, id, count, lane);
+  __syncwarp();
+  if (mine) {
+    const float4 gq = project_bwd_splat<DEG>(rows + lane * P, quat, ga, gb, cam, clamp01);
+    if (dq_vec) {
+      float4* dq = reinterpret_cast<float4*>(d_quats) + id;
+      float4 q4 = *dq;
+      q4.x += gq.x; q4.y += gq.y; q4.z += gq.z; q4.w += gq.w;
+      *dq = q4;
+    } else {
+      d_quats[4 * id + 0] += gq.x;
+      d_quats[4 * id + 1] += gq.y;
+      d_quats[4 * id + 2] += gq.z;
+      d_quats[4 * id + 3] += gq.w;
+    }
+    d_opac[id] += gop;
+  }
+  __syncwarp();
+  // keep the gradient rows' loads below the chain rule: hoisted above it they
+  // would hold a row's worth of registers through it
+  asm volatile("" ::: "memory");
+  scatter_add_rows<3, P>(rows, 0, d_means, id, count, lane);
+  scatter_add_rows<3, P>(rows, 3, d_scales, id, count, lane);
+  if (Row::kVec && sh_vec)
+    scatter_add_rows4<Row::kSh / 4, P>(rows, Row::kShOff, d_sh, id, count, lane);
+  else
+    scatter_add_rows<Row::kSh, P>(rows, Row::kShOff, d_sh, id, count, lane);
+  __syncwarp();   // the rows are reused by the next batch
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float4* __restrict__ quats, const float* __restrict__ sh, int sh_vec, int dq_vec,
+    CamDev cam, int clamp01, const uint32_t* __restrict__ sorted_ids,
+    const float4* __restrict__ g2d, const Header* __restrict__ hdr, float* __restrict__ d_means,
+    float* __restrict__ d_scales, float* __restrict__ d_quats, float* __restrict__ d_opac,
+    float* __restrict__ d_sh) {
+  constexpr int P = BwdRow<DEG>::kPitch;
+  __shared__ __align__(16) float s_rows[kProjBwdWarps][32 * P];
+  __shared__ uint32_t s_queue[kProjBwdWarps][64];
+  const int lane = threadIdx.x & 31;
+  float* rows = s_rows[threadIdx.x >> 5];
+  uint32_t* queue = s_queue[threadIdx.x >> 5];
+  int queued = 0;
   const uint32_t V = hdr->visible;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x)
-    project_bwd_one(means, scales, quats, opac, sh, deg, cam, clamp01, sorted_ids, g2d, r, d_means,
-                    d_scales, d_quats, d_opac, d_sh);
+  const float* g = reinterpret_cast<const float*>(g2d);
+  // base is the same for the whole warp, so every lane runs every iteration
+  for (uint32_t base = blockIdx.x * kProjBwdThreads + (threadIdx.x & ~31u); base < V;
+       base += gridDim.x * kProjBwdThreads) {
+    const uint32_t r = base + lane;
+    bool live = false;
+    if (r < V) {
+      const float4 ga = g2d[3 * r], gb = g2d[3 * r + 1];
+      live = ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f ||
+             gb.y != 0.f || gb.z != 0.f || gb.w != 0.f || g[12 * r + 8] != 0.f;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, live);
+    if (live) queue[queued + __popc(m & lanemask_lt())] = r;
+    queued += __popc(m);
+    __syncwarp();
+    if (queued >= 32) {
+      queued -= 32;
+      project_bwd_batch<DEG>(rows, queue[queued + lane], 32, lane, means, scales, quats, sh,
+                             sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d, d_means, d_scales,
+                             d_quats, d_opac, d_sh);
+    }
+  }
+  if (queued > 0)
+    project_bwd_batch<DEG>(rows, lane < queued ? queue[lane] : 0u, queued, lane, means, scales,
+                           quats, sh, sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d, d_means,
+                           d_scales, d_quats, d_opac, d_sh);
 }
 
 }  // namespace gsr
@@ -516,13 +704,27 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
                                const float* g2d, const Header* hdr, float* d_means,
                                float* d_scales, float* d_quats, float* d_opac, float* d_sh,
                                int num_sms, cudaStream_t st) {
-  int blocks = (n_cap + 127) / 128;
+  (void)opac;
+  int blocks = (n_cap + kProjBwdThreads - 1) / kProjBwdThreads;
   if (blocks == 0) return cudaSuccess;
   if (blocks > num_sms * 16) blocks = num_sms * 16;
-  project_bwd_kernel<<<blocks, 128, 0, st>>>(
-      means, scales, reinterpret_cast<const float4*>(quats), opac, sh, deg, make_cam(cam), clamp01,
-      sorted_ids, reinterpret_cast<const float4*>(g2d), hdr, d_means, d_scales, d_quats, d_opac,
-      d_sh);
+  const int sh_vec = ((uintptr_t)sh & 15) == 0 && ((uintptr_t)d_sh & 15) == 0;
+  const int dq_vec = ((uintptr_t)d_quats & 15) == 0;
+  const CamDev cd = make_cam(cam);
+  const float4* q4 = reinterpret_cast<const float4*>(quats);
+  const float4* g4 = reinterpret_cast<const float4*>(g2d);
+#define GS_PROJECT_BWD(D)                                                                      \
+  project_bwd_kernel<D><<<blocks, kProjBwdThreads, 0, st>>>(means, scales, q4, sh, sh_vec,     \
+                                                            dq_vec, cd, clamp01, sorted_ids,   \
+                                                            g4, hdr, d_means, d_scales,        \
+                                                            d_quats, d_opac, d_sh)
+  switch (deg) {
+    case 0: GS_PROJECT_BWD(0); break;
+    case 1: GS_PROJECT_BWD(1); break;
+    case 2: GS_PROJECT_BWD(2); break;
+    default: GS_PROJECT_BWD(3); break;
+  }
+#undef GS_PROJECT_BWD
   return cudaGetLastError();
 }
 
