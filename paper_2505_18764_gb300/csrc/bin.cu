@@ -159,13 +159,21 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
   }
 }
 
-// Last rank r in [0, V) with offsets[r] <= p (offsets ascend; offsets[0] = 0).
-__device__ __forceinline__ uint32_t rank_of_pair(const uint32_t* __restrict__ offsets, uint32_t V,
-                                                 uint32_t p) {
+// Last rank r in [0, V) with offsets[r] <= p (offsets ascend; offsets[0] = 0),
+// found by the whole warp: each round the 32 lanes probe 32 evenly spaced
+// ranks of the interval, and the ballot of "offsets <= p" (a prefix of the
+// lanes) narrows it 32-fold, so a search over V ranks takes log32 V dependent
+// loads instead of log2 V.  Every lane returns the answer.
+__device__ __forceinline__ uint32_t warp_rank_of_pair(const uint32_t* __restrict__ offsets,
+                                                      uint32_t V, uint32_t p, int lane) {
   uint32_t lo = 0, hi = V;   // answer in [lo, hi)
   while (hi - lo > 1) {
-    const uint32_t mid = lo + (hi - lo) / 2;
-    if (offsets[mid] <= p) lo = mid; else hi = mid;
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t idx = lo + (uint32_t)(lane + 1) * step;
+    const bool le = idx < hi && offsets[idx] <= p;
+    const uint32_t cnt = (uint32_t)__popc(__ballot_sync(0xffffffffu, le));
+    hi = min(hi, lo + (cnt + 1) * step);
+    lo += cnt * step;
   }
   return lo;
 }
@@ -228,8 +236,13 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
     const uint32_t p0 = pbase + c * kEmitChunk;         // global pair indices [p0, p1)
     const uint32_t p1 = pbase + min(P, (c + 1) * kEmitChunk);
     __syncthreads();
-    if (tid == 0) s_r0 = rank_of_pair(offsets, V, p0);
-    if (tid == 32) s_r1 = rank_of_pair(offsets, V, p1 - 1);
+    if (tid < 32) {
+      const uint32_t r = warp_rank_of_pair(offsets, V, p0, tid);
+      if (tid == 0) s_r0 = r;
+    } else if (tid < 64) {
+      const uint32_t r = warp_rank_of_pair(offsets, V, p1 - 1, tid - 32);
+      if (tid == 32) s_r1 = r;
+    }
     __syncthreads();
     const uint32_t r0 = s_r0;
     // ranks overlapping [p0, p1): each has >= 1 pair, so at most kEmitChunk of them

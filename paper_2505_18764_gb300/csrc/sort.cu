@@ -24,7 +24,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr unsigned long long kFlagAgg = 1ull << 30;
 constexpr unsigned long long kFlagPre = 2ull << 30;
 constexpr unsigned long long kCount30 = (1ull << 30) - 1;
-constexpr int kLookWindow = 8;   // look-back words read per round trip
+constexpr int kLookWindow = 4;   // look-back words read per round trip
 
 __device__ __forceinline__ unsigned long long make_status(uint32_t tag, unsigned long long flag,
                                                           uint32_t count) {
