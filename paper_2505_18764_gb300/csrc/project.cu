@@ -243,7 +243,7 @@ __device__ __forceinline__ uint32_t project_splat(
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kProjThreads, 3) project_fwd_kernel(
+__global__ void __launch_bounds__(kProjThreads, 2) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float4* __restrict__ quats, const float* __restrict__ opac,
     const float* __restrict__ sh, int n, CamDev cam, int clamp01, int sh_vec,
@@ -279,13 +279,26 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_fwd_kernel(
     }
   };
   const int64_t warps_total = (int64_t)gridDim.x * kProjWarps;
-  for (int64_t base = ((int64_t)blockIdx.x * kProjWarps + warp) * 32; base < n;
-       base += warps_total * 32) {
+  // the cheap test's inputs of the warp's next 32 splats are loaded one step
+  // ahead, so their DRAM latency overlaps the current step
+  struct Cheap { float mx, my, mz, o, sx, sy, sz; };
+  auto load_cheap = [&](int64_t b) {
+    Cheap c{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int64_t i = b + lane;
+    if (i < n) {
+      c.mx = means[3 * i]; c.my = means[3 * i + 1]; c.mz = means[3 * i + 2];
+      c.o = opac[i];
+      c.sx = scales[3 * i]; c.sy = scales[3 * i + 1]; c.sz = scales[3 * i + 2];
+    }
+    return c;
+  };
+  int64_t base = ((int64_t)blockIdx.x * kProjWarps + warp) * 32;
+  Cheap cur = load_cheap(base);
+  for (; base < n; base += warps_total * 32) {
+    const Cheap nxt = load_cheap(base + warps_total * 32);
     const int i = (int)base + lane;
     bool cand = false;
-    if (i < n)
-      cand = may_be_visible(cam, means[3 * i], means[3 * i + 1], means[3 * i + 2], opac[i],
-                            scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]);
+    if (i < n) cand = may_be_visible(cam, cur.mx, cur.my, cur.mz, cur.o, cur.sx, cur.sy, cur.sz);
     if (i < n && !cand) keys[i] = kNone;
     const uint32_t m = __ballot_sync(0xffffffffu, cand);
     if (cand) q[queued + __popc(m & lanemask_lt())] = i;
@@ -298,6 +311,7 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_fwd_kernel(
       if (lane < queued) q[lane] = q[32 + lane];
       __syncwarp();
     }
+    cur = nxt;
   }
   project_queued(queued);
   // visible count: warp-aggregate, one atomic per warp
@@ -678,7 +692,7 @@ cudaError_t launch_project_fwd(const float* means, const float* scales, const fl
                                uint32_t* keys, Header* hdr, uint2* ranges, int n_ranges,
                                uint32_t* epoch, int num_sms, cudaStream_t st) {
   int blocks = (n + kProjThreads - 1) / kProjThreads;
-  const int cap = num_sms * 8;  // persistent: a few waves' worth of CTAs
+  const int cap = num_sms * 2;  // persistent: one wave, two CTAs per SM (the launch bound)
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   const float4* q4 = reinterpret_cast<const float4*>(quats);
