@@ -317,6 +317,43 @@ def test_backward_dense_with_t_culling():
     _check_backward(scene_np, cam, gs.RasterOpts(sh_degree=1, t_cull=1e-2), g)
 
 
+def _offset_view(t, off=1):
+    """A contiguous copy of t whose storage starts `off` floats past a 16-byte
+    boundary (torch allocations are 256-byte aligned)."""
+    flat = torch.zeros(t.numel() + off, dtype=t.dtype, device=t.device)
+    v = flat[off:].view(t.shape)
+    v.copy_(t)
+    return v
+
+
+@pytest.mark.parametrize("deg", [1, 3])
+def test_project_backward_unaligned_rows(deg):
+    """The backward projection moves SH rows and quaternion gradients as 16-byte
+    words when the arrays are 16-byte aligned and word by word otherwise: from
+    the same per-splat 2D sums both give bit-identical gradients, and added into
+    non-zero buffers they accumulate."""
+    scene_np = syn.cube_scene(3000, seed=95 + deg, sh_degree=deg, hi_sigma=0.1)
+    cam = syn.look_at((0.4, -0.3, -3.5), (0.0, 0.0, 0.0), 50.0, 97, 83)
+    g = syn.uniform_image(cam.height, cam.width, seed=96, lo=-1.0, hi=1.0)
+    opts = gs.RasterOpts(sh_degree=deg)
+    scene, ws, out = run_forward(scene_np, cam, opts)
+    gs.blend_backward(ws, cam, opts, out["state"], out["last"],
+                      torch.as_tensor(g, dtype=torch.float32).contiguous().cuda())
+    aligned = gs.project_backward(ws, scene, cam, opts, gs.zero_grads(scene))
+    shifted = gs.SceneTensors(scene.means, scene.scales, scene.quats, scene.opacities,
+                              _offset_view(scene.sh), scene.sh_degree)
+    base = {k: torch.full_like(v, 0.25) for k, v in gs.zero_grads(scene).items()}
+    unaligned = gs.project_backward(ws, shifted, cam, opts, {k: _offset_view(v) for k, v in base.items()})
+    gs.check_status(ws)
+    torch.cuda.synchronize()
+    assert scene.sh.data_ptr() % 16 == 0 and shifted.sh.data_ptr() % 16 == 4
+    for k in GROUPS:
+        a = aligned[k].cpu().numpy()
+        assert np.abs(a).max() > 0, k
+        b = unaligned[k].cpu().numpy()
+        assert np.array_equal(b, a + np.float32(0.25)), k
+
+
 @pytest.mark.parametrize("mode,thr", [("naive", 0), ("warp", 8), ("warp", 33), ("warp", 1)])
 def test_reduction_modes_agree(mode, thr):
     """The reduction is exactly a sum: every mode gives the same per-splat
