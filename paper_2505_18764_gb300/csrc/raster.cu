@@ -785,39 +785,6 @@ __global__ void __launch_bounds__(1024) item_order_kernel(const uint32_t* __rest
   }
 }
 
-// ---------------------------------------------------------------------------
-// Summed L1 / L2 image loss and its gradient.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ img,
-                                                   const float* __restrict__ tgt, int64_t n,
-                                                   int kind, float* __restrict__ grad,
-                                                   double* __restrict__ loss) {
-  __shared__ double s_w[8];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = img[i] - tgt[i];
-    float g;
-    if (kind == GS_LOSS_L1) {
-      acc += fabsf(d);
-      g = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-    } else {
-      acc += (double)d * d;
-      g = 2.f * d;
-    }
-    if (grad) grad[i] = g;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
-    atomicAdd(loss, t);
-  }
-}
-
 namespace {
 // Resident CTAs per SM of `kernel` at kThreads.
 template <typename K>
@@ -873,17 +840,6 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
         threshold, back, chunk_state, chunk_in, chunk_out);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_loss(const float* img, const float* tgt, int64_t n, int kind, float* grad,
-                        double* loss, int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), st);
-  if (e != cudaSuccess) return e;
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > num_sms * 4) blocks = num_sms * 4;
-  if (blocks < 1) blocks = 1;
-  loss_kernel<<<(int)blocks, 256, 0, st>>>(img, tgt, n, kind, grad, loss);
   return cudaGetLastError();
 }
 
