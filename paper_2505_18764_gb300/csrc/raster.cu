@@ -748,41 +748,50 @@ __device__ __forceinline__ int cost_bucket(uint32_t c) {
   return kCostBuckets - 2 - min(lg * 4 + frac, kCostBuckets - 2);
 }
 
-__global__ void __launch_bounds__(1024) item_order_kernel(const uint32_t* __restrict__ items,
-                                                         const uint32_t* __restrict__ cost,
-                                                         const Header* __restrict__ hdr,
-                                                         uint32_t* __restrict__ out) {
-  __shared__ uint32_t s_cnt[kCostBuckets];
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderWarps = kOrderThreads / 32;
+
+__global__ void __launch_bounds__(kOrderThreads) item_order_kernel(
+    const uint32_t* __restrict__ items, const uint32_t* __restrict__ cost,
+    const Header* __restrict__ hdr, uint32_t* __restrict__ out) {
+  // per-warp bucket counts, then per-warp placement cursors
+  __shared__ uint32_t s_cnt[kOrderWarps][kCostBuckets];
+  __shared__ uint32_t s_part[kCostBuckets / 32];
   const uint32_t n = hdr->n_items;
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < kCostBuckets; i += blockDim.x) s_cnt[i] = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kOrderWarps * kCostBuckets; i += kOrderThreads)
+    (&s_cnt[0][0])[i] = 0u;
   __syncthreads();
-  // lanes with the same bucket add together (most items share a few buckets)
-  const uint32_t n_pad = (n + 31u) & ~31u;
-  for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
-    const int bkt = i < n ? cost_bucket(cost[i]) : -1;
-    const uint32_t peers = __match_any_sync(kFull, bkt);
-    if (bkt >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[bkt], (uint32_t)__popc(peers));
+#pragma unroll 4
+  for (uint32_t i = threadIdx.x; i < n; i += kOrderThreads)
+    atomicAdd(&s_cnt[warp][cost_bucket(cost[i])], 1u);
+  __syncthreads();
+  // exclusive scan in (bucket, warp) order; thread b < kCostBuckets owns bucket b
+  uint32_t tot = 0;
+  if (threadIdx.x < kCostBuckets) {
+    for (int w = 0; w < kOrderWarps; ++w) tot += s_cnt[w][threadIdx.x];
   }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (threadIdx.x < kCostBuckets && lane == 31) s_part[warp] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < kCostBuckets; ++i) {
-      const uint32_t c = s_cnt[i];
-      s_cnt[i] = run;
+  if (threadIdx.x < kCostBuckets) {
+    uint32_t run = incl - tot;
+    for (int w = 0; w < warp; ++w) run += s_part[w];
+    for (int w = 0; w < kOrderWarps; ++w) {
+      const uint32_t c = s_cnt[w][threadIdx.x];
+      s_cnt[w][threadIdx.x] = run;
       run += c;
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
-    const int bkt = i < n ? cost_bucket(cost[i]) : -1;
-    const uint32_t peers = __match_any_sync(kFull, bkt);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (bkt >= 0 && lane == leader) base = atomicAdd(&s_cnt[bkt], (uint32_t)__popc(peers));
-    base = __shfl_sync(kFull, base, leader);
-    if (bkt >= 0) out[base + __popc(peers & lanemask_lt())] = items[i];
-  }
+#pragma unroll 4
+  for (uint32_t i = threadIdx.x; i < n; i += kOrderThreads)
+    out[atomicAdd(&s_cnt[warp][cost_bucket(cost[i])], 1u)] = items[i];
 }
 
 namespace {
@@ -824,7 +833,7 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  item_order_kernel<<<1, 1024, 0, st>>>(fwd_items, item_cost, hdr, items);
+  item_order_kernel<<<1, kOrderThreads, 0, st>>>(fwd_items, item_cost, hdr, items);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mode == GS_REDUCE_NAIVE) {
