@@ -60,9 +60,21 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
       const int j = k * kBinThreads + tid;
       const uint32_t r = base + j;
       uint32_t cnt = 0;
+      const uint32_t id = r < V ? sorted_ids[r] : 0u;
+      // the warp's 32 consecutive ranks move their 48-byte records together:
+      // consecutive lanes take consecutive 16-byte words of the 32 records
+      {
+        const uint32_t r0 = r - (uint32_t)lane;
+        const float4* src = reinterpret_cast<const float4*>(rec);
+        float4* dst = reinterpret_cast<float4*>(rec_sorted);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int w = t * 32 + lane, q = w / 3, part = w % 3;
+          const uint32_t idq = __shfl_sync(0xffffffffu, id, q);
+          if (r0 + q < V) dst[(size_t)(r0 + q) * 3 + part] = src[(size_t)idq * 3 + part];
+        }
+      }
       if (r < V) {
-        const uint32_t id = sorted_ids[r];
-        rec_sorted[r] = rec[id];
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         g2d[3 * (size_t)r] = z;
         g2d[3 * (size_t)r + 1] = z;
@@ -323,53 +335,72 @@ __device__ __forceinline__ uint32_t block_items(uint32_t len, uint32_t split) {
   return len >= 8u * (uint64_t)split ? 16u : (len >= split ? 8u : 4u);
 }
 
-__global__ void __launch_bounds__(1024) block_order_kernel(const uint2* __restrict__ ranges,
-                                                          int nblocks, uint32_t split,
-                                                          uint32_t* __restrict__ items,
-                                                          Header* __restrict__ hdr) {
-  __shared__ uint32_t s_cnt[kOrderBuckets];
-  __shared__ uint32_t s_pos[kOrderBuckets];
-  const int lane = threadIdx.x & 31;
-  const int nb_pad = (nblocks + 31) & ~31;
-  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0;
+constexpr int kBlockOrderThreads = 1024;
+constexpr int kBlockOrderWarps = kBlockOrderThreads / 32;
+constexpr int kBlockOrderPer = 8;   // blocks per thread held in registers (8192 blocks)
+
+__global__ void __launch_bounds__(kBlockOrderThreads) block_order_kernel(
+    const uint2* __restrict__ ranges, int nblocks, uint32_t split, uint32_t* __restrict__ items,
+    Header* __restrict__ hdr) {
+  // per-warp item counts per bucket, then per-warp placement cursors
+  __shared__ uint32_t s_cnt[kBlockOrderWarps][kOrderBuckets];
+  __shared__ uint32_t s_part[kOrderBuckets / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kBlockOrderWarps * kOrderBuckets; i += kBlockOrderThreads)
+    (&s_cnt[0][0])[i] = 0u;
   __syncthreads();
-  // lanes with the same bucket and item count add together
-  for (int b = threadIdx.x; b < nb_pad; b += blockDim.x) {
-    const uint32_t len = b < nblocks ? ranges[b].y - ranges[b].x : 0u;
-    const int bkt = b < nblocks ? length_bucket(len) : -1;
-    const uint32_t peers = __match_any_sync(0xffffffffu, bkt * 32 + (int)block_items(len, split));
-    if (bkt >= 0 && lane == __ffs(peers) - 1)
-      atomicAdd(&s_cnt[bkt], block_items(len, split) * (uint32_t)__popc(peers));
+  // the lengths of this thread's blocks (any beyond kBlockOrderPer per thread are re-read)
+  uint32_t len_r[kBlockOrderPer];
+#pragma unroll
+  for (int k = 0; k < kBlockOrderPer; ++k) {
+    const int b = threadIdx.x + k * kBlockOrderThreads;
+    len_r[k] = b < nblocks ? ranges[b].y - ranges[b].x : 0u;
+  }
+  auto len_of = [&](int b, int k) {
+    return k < kBlockOrderPer ? len_r[k] : ranges[b].y - ranges[b].x;
+  };
+  for (int b = threadIdx.x, k = 0; b < nblocks; b += kBlockOrderThreads, ++k) {
+    const uint32_t len = len_of(b, k);
+    atomicAdd(&s_cnt[warp][length_bucket(len)], block_items(len, split));
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < kOrderBuckets; ++i) {
-      s_pos[i] = run;
-      run += s_cnt[i];
+  // exclusive scan in (bucket, warp) order; thread t < kOrderBuckets owns bucket t
+  uint32_t tot = 0;
+  if (threadIdx.x < kOrderBuckets) {
+    for (int w = 0; w < kBlockOrderWarps; ++w) tot += s_cnt[w][threadIdx.x];
+  }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (threadIdx.x < kOrderBuckets && lane == 31) s_part[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets) {
+    uint32_t run = incl - tot;
+    for (int w = 0; w < warp; ++w) run += s_part[w];
+    for (int w = 0; w < kBlockOrderWarps; ++w) {
+      const uint32_t c = s_cnt[w][threadIdx.x];
+      s_cnt[w][threadIdx.x] = run;
+      run += c;
     }
-    hdr->n_items = run;
+    if (threadIdx.x == kOrderBuckets - 1) hdr->n_items = run;
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nb_pad; b += blockDim.x) {
-    const uint32_t len = b < nblocks ? ranges[b].y - ranges[b].x : 0u;
-    const int bkt = b < nblocks ? length_bucket(len) : -1;
+  for (int b = threadIdx.x, k = 0; b < nblocks; b += kBlockOrderThreads, ++k) {
+    const uint32_t len = len_of(b, k);
     const uint32_t n = block_items(len, split);
-    const uint32_t peers = __match_any_sync(0xffffffffu, bkt * 32 + (int)n);
-    const int leader = __ffs(peers) - 1;
-    uint32_t pos = 0;
-    if (bkt >= 0 && lane == leader) pos = atomicAdd(&s_pos[bkt], n * (uint32_t)__popc(peers));
-    pos = __shfl_sync(0xffffffffu, pos, leader) + n * (uint32_t)__popc(peers & lanemask_lt());
-    if (bkt < 0) continue;
+    const uint32_t pos = atomicAdd(&s_cnt[warp][length_bucket(len)], n);
     const uint32_t code0 = n == 16u ? 16u : (n == 8u ? 8u : 0u);
-    for (uint32_t k = 0; k < n; ++k) items[pos + k] = ((uint32_t)b << 5) | (code0 + k);
+    for (uint32_t j = 0; j < n; ++j) items[pos + j] = ((uint32_t)b << 5) | (code0 + j);
   }
 }
 
 cudaError_t launch_block_order(const uint2* ranges, int nblocks, uint32_t split, uint32_t* items,
                                Header* hdr, cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
-  block_order_kernel<<<1, 1024, 0, st>>>(ranges, nblocks, split, items, hdr);
+  block_order_kernel<<<1, kBlockOrderThreads, 0, st>>>(ranges, nblocks, split, items, hdr);
   return cudaGetLastError();
 }
 
