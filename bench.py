@@ -485,14 +485,12 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
 
     # The same step scheduled as a training loop would: step k+1's target is
     # copied up on a copy stream into the other of two buffers while step k
-    # computes, and the gradients are zeroed on a side stream while the
-    # forward half runs (the backward waits for both).  Every step still copies
-    # its own target up and reads its loss back inside the timed region.
+    # computes, and the gradient rows the previous view's backward wrote (its
+    # visible splats) are zeroed instead of all n rows.  Every step still
+    # copies its own target up and reads its loss back inside the timed region.
     copy_st = torch.cuda.Stream(dev)
-    zero_st = torch.cuda.Stream(dev)
     tgt_buf = [target, torch.empty_like(target)]
     copied = [torch.cuda.Event(), torch.cuda.Event()]
-    zeroed = torch.cuda.Event()
 
     def issue_copy(k):
         copy_st.wait_stream(stream)   # the buffer's previous reader (step k - 2's loss) is done
@@ -501,11 +499,7 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
         copied[k % 2].record(copy_st)
 
     def step_pipelined(k, last_k):
-        zero_st.wait_stream(stream)   # the previous backward is done with the gradients
-        with torch.cuda.stream(zero_st):
-            for g in gnames:
-                grads[g].zero_()
-        zeroed.record(zero_st)
+        gs.zero_touched_gradients(ws, grads, stream)   # rows of the previous view
         if k + 1 <= last_k:
             issue_copy(k + 1)
         stream.wait_event(copied[k % 2])
@@ -513,11 +507,12 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
         gs.sort(ws, stream)
         gs.raster_forward(ws, ccam, opts, image, state, last, None, stream=stream)
         gs.loss(image, tgt_buf[k % 2], "l1", dl, loss, stream)
-        stream.wait_event(zeroed)
         gs.raster_backward(ws, scene, ccam, opts, state, last, dl, grads, stream)
         host_loss.copy_(loss, non_blocking=True)
 
     def timed_pipelined():
+        for g in gnames:
+            grads[g].zero_()
         issue_copy(0)
         for k in range(args.warmup):
             step_pipelined(k, args.warmup - 1)
@@ -570,10 +565,11 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
                 h2d_bytes_per_step=host_tgt.numel() * host_tgt.element_size(),
                 d2h_bytes_per_step=host_loss.numel() * host_loss.element_size(), steps=K,
                 inputs="target image up, loss down; scene parameters resident",
-                schedule="next target copied up during the step, gradients zeroed beside "
-                         "the forward half",
+                schedule="next target copied up during the step; the gradient rows the "
+                         "previous view wrote are zeroed (gs_zero_touched_gradients)",
                 serial=dict(value=v1, unit="ms/view",
-                            schedule="copy up, zero gradients, step, loss down, in one stream"),
+                            schedule="copy up, zero all gradient rows, step, loss down, in one "
+                                     "stream"),
                 stateless=dict(value=v2, unit="ms/view",
                                h2d_bytes_per_step=sum(t.numel() * t.element_size() for t in host_in),
                                d2h_bytes_per_step=sum(t.numel() * t.element_size() for t in host_out)))

@@ -306,6 +306,23 @@ def raster_backward(ws: Workspace, scene: SceneTensors, cam, opts: RasterOpts, s
     return grads
 
 
+def zero_touched_gradients(ws: Workspace, grads: dict, stream=None) -> dict:
+    """Zeroes the gradient rows of the splats the last sort on ws ordered (the
+    rows a backward on that view adds to); buffers that were all zero before
+    that backward are all zero again.  Call before the next sort on ws."""
+    n = int(grads["means"].shape[0])
+    K = (int(ws.c.sh_degree) + 1) ** 2
+    shapes = dict(means=(n, 3), scales=(n, 3), quats=(n, 4), opacities=(n,), sh=(n, K, 3))
+    for k, shp in shapes.items():
+        if tuple(grads[k].shape) != shp:
+            raise ValueError(f"grads[{k!r}] must have shape {shp}")
+    check(_lib.load().gs_zero_touched_gradients(
+        ws.ref, n, _f32(grads["means"], "d_means"), _f32(grads["scales"], "d_scales"),
+        _f32(grads["quats"], "d_quats"), _f32(grads["opacities"], "d_opacities"),
+        _f32(grads["sh"], "d_sh"), _stream(stream)), "gs_zero_touched_gradients")
+    return grads
+
+
 def loss(image, target, kind: str = "l2", dL_dimage=None, loss_out=None, stream=None):
     """Summed L1 / L2 loss; returns (dL_dimage, loss as a 1-element float64 tensor)."""
     if dL_dimage is None:

@@ -96,6 +96,8 @@ _SIGS = {
                       c_int32, c_void_p],
     "gs_sort_pairs_noalloc": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p],
     "gs_fp32_fma_rate": [c_int32, POINTER(c_double), c_void_p],
+    "gs_zero_touched_gradients": [POINTER(GsWorkspace), c_int32, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p],
 }
 
 EXPORTED = tuple(_SIGS) + ("gs_last_error",)

@@ -18,6 +18,8 @@ cudaError_t launch_project_bwd(const float*, const float*, const float*, const f
                                int, int, const gs_camera&, int, const uint32_t*, const float*,
                                const Header*, float*, float*, float*, float*, float*, int,
                                cudaStream_t);
+cudaError_t launch_zero_touched(int, int, const uint32_t*, const Header*, float*, float*, float*,
+                                float*, float*, int, cudaStream_t);
 cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,
                                  const uint32_t*, uint32_t, uint32_t, uint32_t, int, uint32_t,
                                  const uint32_t*, unsigned long long*, uint32_t*, const uint32_t*,
@@ -525,6 +527,21 @@ int gs_project_backward(gs_workspace* ws, const float* means, const float* scale
                              at<Header>(ws, L_HDR), d_means, d_scales, d_quats, d_opacities, d_sh,
                              num_sms(), reinterpret_cast<cudaStream_t>(stream)),
           "projection backward kernel");
+  return GS_OK;
+}
+
+int gs_zero_touched_gradients(gs_workspace* ws, int32_t n, float* d_means, float* d_scales,
+                              float* d_quats, float* d_opacities, float* d_sh,
+                              gs_stream_t stream) {
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
+  if (n > 0 && (!d_means || !d_scales || !d_quats || !d_opacities || !d_sh))
+    return fail(GS_ERR_INVALID_ARG, "null gradient pointer");
+  GS_CUDA(launch_zero_touched(ws->n, ws->sh_degree, at<uint32_t>(ws, L_VB), at<Header>(ws, L_HDR),
+                              d_means, d_scales, d_quats, d_opacities, d_sh, num_sms(),
+                              reinterpret_cast<cudaStream_t>(stream)),
+          "gradient zeroing kernel");
   return GS_OK;
 }
 

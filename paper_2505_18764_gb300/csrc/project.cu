@@ -669,6 +669,59 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
                            d_scales, d_quats, d_opac, d_sh);
 }
 
+// Zeroing of the gradient rows of the last depth order's splats (the rows a
+// backward on that view adds to), with the same warp-wide row layout as the
+// copies above: an instruction writes consecutive words of the warp's rows.
+template <int LEN>
+__device__ __forceinline__ void zero_rows(float* __restrict__ dst, uint32_t id, int count,
+                                          int lane) {
+#pragma unroll 4
+  for (int t = 0; t < LEN; ++t) {
+    const int i = t * 32 + lane, j = i / LEN, c = i % LEN;
+    const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+    if (j < count) dst[(size_t)idj * LEN + c] = 0.f;
+  }
+}
+
+template <int LEN4>
+__device__ __forceinline__ void zero_rows4(float* __restrict__ dst, uint32_t id, int count,
+                                           int lane) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll 4
+  for (int t = 0; t < LEN4; ++t) {
+    const int i = t * 32 + lane, j = i / LEN4, c = i % LEN4;
+    const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+    if (j < count) d4[(size_t)idj * LEN4 + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) zero_touched_kernel(
+    const uint32_t* __restrict__ sorted_ids, const Header* __restrict__ hdr, int sh_vec,
+    int dq_vec, float* __restrict__ d_means, float* __restrict__ d_scales,
+    float* __restrict__ d_quats, float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  constexpr int kSh = 3 * (DEG + 1) * (DEG + 1);
+  const uint32_t V = hdr->visible;
+  const int lane = threadIdx.x & 31;
+  // base is the same for the whole warp
+  for (uint32_t base = blockIdx.x * 256u + (threadIdx.x & ~31u); base < V;
+       base += gridDim.x * 256u) {
+    const int count = (int)min(32u, V - base);
+    const uint32_t id = lane < count ? sorted_ids[base + lane] : 0u;
+    zero_rows<3>(d_means, id, count, lane);
+    zero_rows<3>(d_scales, id, count, lane);
+    zero_rows<1>(d_opac, id, count, lane);
+    if (dq_vec)
+      zero_rows4<1>(d_quats, id, count, lane);
+    else
+      zero_rows<4>(d_quats, id, count, lane);
+    if (kSh % 4 == 0 && sh_vec)
+      zero_rows4<(kSh % 4 == 0 ? kSh / 4 : 1)>(d_sh, id, count, lane);
+    else
+      zero_rows<kSh>(d_sh, id, count, lane);
+  }
+}
+
 }  // namespace gsr
 
 // Host launchers (called from api.cu)
@@ -739,6 +792,28 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
     default: GS_PROJECT_BWD(3); break;
   }
 #undef GS_PROJECT_BWD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_touched(int n_cap, int deg, const uint32_t* sorted_ids,
+                                const Header* hdr, float* d_means, float* d_scales,
+                                float* d_quats, float* d_opac, float* d_sh, int num_sms,
+                                cudaStream_t st) {
+  int blocks = (n_cap + 255) / 256;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > num_sms * 8) blocks = num_sms * 8;
+  const int sh_vec = ((uintptr_t)d_sh & 15) == 0;
+  const int dq_vec = ((uintptr_t)d_quats & 15) == 0;
+#define GS_ZERO_TOUCHED(D)                                                                      \
+  zero_touched_kernel<D><<<blocks, 256, 0, st>>>(sorted_ids, hdr, sh_vec, dq_vec, d_means,      \
+                                                 d_scales, d_quats, d_opac, d_sh)
+  switch (deg) {
+    case 0: GS_ZERO_TOUCHED(0); break;
+    case 1: GS_ZERO_TOUCHED(1); break;
+    case 2: GS_ZERO_TOUCHED(2); break;
+    default: GS_ZERO_TOUCHED(3); break;
+  }
+#undef GS_ZERO_TOUCHED
   return cudaGetLastError();
 }
 

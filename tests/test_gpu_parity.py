@@ -354,6 +354,41 @@ def test_project_backward_unaligned_rows(deg):
         assert np.array_equal(b, a + np.float32(0.25)), k
 
 
+@pytest.mark.parametrize("deg", [0, 2, 3])
+def test_zero_touched_gradients(deg):
+    """Zeroing the last depth order's rows undoes a backward into zero buffers
+    exactly, and leaves the buffers ready for the next view: a backward of a
+    second view after it matches that view's gradients from fresh buffers."""
+    scene_np = syn.cube_scene(3000, seed=97 + deg, sh_degree=deg, hi_sigma=0.1)
+    # two narrow views on different corners of the cube: each sees about half
+    cams = [syn.look_at((0.5, 0.2, -2.0), (0.6, 0.4, 0.0), 30.0, 96, 80),
+            syn.look_at((-0.5, -0.3, -2.0), (-0.6, -0.4, 0.0), 30.0, 96, 80)]
+    opts = gs.RasterOpts(sh_degree=deg)
+    scene = gs.SceneTensors.from_numpy(scene_np)
+    ws = gs.Workspace(scene.n, 96, 80, opts)
+    g = torch.as_tensor(syn.uniform_image(80, 96, seed=98, lo=-1.0, hi=1.0)).contiguous().cuda()
+
+    def view(cam, grads):
+        out = gs.render(ws, scene, cam, opts)
+        gs.raster_backward(ws, scene, cam, opts, out["state"], out["last"], g, grads)
+        gs.check_status(ws)
+        return grads
+
+    grads = view(cams[0], gs.zero_grads(scene))
+    V = gs.read_counters(ws)["visible"]
+    assert 0 < V < scene.n
+    assert all(float(grads[k].abs().sum()) > 0 for k in GROUPS)
+    gs.zero_touched_gradients(ws, grads)
+    torch.cuda.synchronize()
+    for k in GROUPS:
+        assert int(torch.count_nonzero(grads[k])) == 0, k
+    second = view(cams[1], grads)
+    fresh = view(cams[1], gs.zero_grads(scene))
+    for k in GROUPS:
+        a, b = second[k].cpu().numpy(), fresh[k].cpu().numpy()
+        assert rel_l2(a.astype(np.float64), b.astype(np.float64)) < 1e-5, k
+
+
 @pytest.mark.parametrize("mode,thr", [("naive", 0), ("warp", 8), ("warp", 33), ("warp", 1)])
 def test_reduction_modes_agree(mode, thr):
     """The reduction is exactly a sum: every mode gives the same per-splat
