@@ -91,7 +91,7 @@ typedef struct gs_camera {
   float znear;
 } gs_camera;
 
-#define GS_SPLIT_THRESHOLD_DEFAULT 768
+#define GS_SPLIT_THRESHOLD_DEFAULT 1536
 #define GS_REDUCE_THRESHOLD_DEFAULT 16
 
 typedef struct gs_raster_opts {

@@ -22,7 +22,7 @@ GS_ERR_CUDA = -4
 
 GS_STATE_FP32, GS_STATE_FP16, GS_STATE_UNORM16, GS_STATE_UNORM8 = 0, 1, 2, 3
 GS_REDUCE_WARP, GS_REDUCE_NAIVE = 0, 1
-GS_SPLIT_THRESHOLD_DEFAULT = 768
+GS_SPLIT_THRESHOLD_DEFAULT = 1536
 GS_REDUCE_THRESHOLD_DEFAULT = 16
 GS_BWD_FRONT_TO_BACK, GS_BWD_BACK_TO_FRONT = 0, 1
 GS_MODE_FORWARD, GS_MODE_FORWARD_BACKWARD = 0, 1
