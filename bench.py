@@ -215,9 +215,41 @@ def run_ours(args, rank, world, local_rank):
     if args.ablation_only:
         return dict(metric=METRIC, reduction_ablation=run_ablation(gs, torch, ws, ccam, state32, last,
                                                                    dl, stream, None, reps=1))
+    # stage times: the same step as separate calls, events between the stages
+    eager_ms, per_stage, _, _ = timed(step32, args.steps, 0)
+
+    # the headline: each view as one gs_render_batch_graph call (the step's
+    # launches captured into a CUDA graph, updated in place from view to view)
+    gstream = torch.cuda.Stream(dev)
+    gout = dict(image=image, state=state32, last=last, dL_dimage=dl, loss=loss, grads=grads)
+
+    def graph_step():
+        gs.render_batch([gs.Request(scene, ccam, opts, backward=True, loss_kind="l1",
+                                    target=target, outputs=gout)], ws, gstream, graph=True)
+
+    def timed_graph(K, W_):
+        gstream.wait_stream(stream)
+        with torch.cuda.stream(gstream):
+            for _ in range(W_):
+                graph_step()
+        torch.cuda.synchronize(dev)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(gstream):
+            for k in range(K):
+                ev[k][0].record(gstream)
+                graph_step()
+                ev[k][1].record(gstream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        return (ev[0][0].elapsed_time(ev[-1][1]), [e[0].elapsed_time(e[1]) for e in ev], t_wall)
+
     if not args.no_extras:
         clocks.start()
-    total_ms, per_stage, step_ms, t_wall = timed(step32, args.steps, 0)
+    total_ms, step_ms, t_wall = timed_graph(args.steps, max(args.warmup, 2))
     clk = clocks.stop() if not args.no_extras else None
     gs.check_status(ws, stream)
     total_ms_max = max_over_ranks_ms(total_ms, dev, world)
@@ -296,6 +328,8 @@ def run_ours(args, rank, world, local_rank):
                counts=dict(visible=V, pairs=P, live_pairs=P_live, fragments=F, in_front=n_front,
                            pixels=npix),
                splat_frags_per_s=round(F / (ms_per_view * 1e-3), 1),
+               schedule="one gs_render_batch_graph call per view (the step as one CUDA graph)",
+               eager_ms_per_view=round(eager_ms / args.steps, 4),
                stages_ms=per_stage, stage_roofline=stage_roof,
                p50_ms=round(float(np.percentile(step_ms, 50)), 4),
                p99_ms=round(float(np.percentile(step_ms, 99)), 4),
@@ -310,7 +344,7 @@ def run_ours(args, rank, world, local_rank):
         st16 = gs.alloc_state(H, W, "fp16", dev)
         tot16, per16, _, _ = timed(make_step(ws16, o16, st16), args.steps, args.warmup)
         res["fp16_state"] = dict(ms_per_view=round(tot16 / args.steps, 4),
-                                 speedup_vs_fp32=round((total_ms / args.steps) / (tot16 / args.steps), 4),
+                                 speedup_vs_fp32=round((eager_ms / args.steps) / (tot16 / args.steps), 4),
                                  stages_ms=per16)
         del ws16
         res["e2e"] = run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, state32,
@@ -488,42 +522,46 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
     # computes, and the gradient rows the previous view's backward wrote (its
     # visible splats) are zeroed instead of all n rows.  Every step still
     # copies its own target up and reads its loss back inside the timed region.
+    # The step is one gs_render_batch_graph call (a CUDA graph) on its own stream.
+    st = torch.cuda.Stream(dev)
     copy_st = torch.cuda.Stream(dev)
     tgt_buf = [target, torch.empty_like(target)]
     copied = [torch.cuda.Event(), torch.cuda.Event()]
+    gout = dict(image=image, state=state, last=last, dL_dimage=dl, loss=loss, grads=grads)
 
     def issue_copy(k):
-        copy_st.wait_stream(stream)   # the buffer's previous reader (step k - 2's loss) is done
+        copy_st.wait_stream(st)   # the buffer's previous reader (step k - 2's loss) is done
         with torch.cuda.stream(copy_st):
             tgt_buf[k % 2].copy_(host_tgt, non_blocking=True)
         copied[k % 2].record(copy_st)
 
     def step_pipelined(k, last_k):
-        gs.zero_touched_gradients(ws, grads, stream)   # rows of the previous view
+        gs.zero_touched_gradients(ws, grads, st)   # rows of the previous view
         if k + 1 <= last_k:
             issue_copy(k + 1)
-        stream.wait_event(copied[k % 2])
-        gs.project(ws, scene, ccam, opts, stream)
-        gs.sort(ws, stream)
-        gs.raster_forward(ws, ccam, opts, image, state, last, None, stream=stream)
-        gs.loss(image, tgt_buf[k % 2], "l1", dl, loss, stream)
-        gs.raster_backward(ws, scene, ccam, opts, state, last, dl, grads, stream)
-        host_loss.copy_(loss, non_blocking=True)
+        st.wait_event(copied[k % 2])
+        gs.render_batch([gs.Request(scene, ccam, opts, backward=True, loss_kind="l1",
+                                    target=tgt_buf[k % 2], outputs=gout)], ws, st, graph=True)
+        with torch.cuda.stream(st):
+            host_loss.copy_(loss, non_blocking=True)
 
     def timed_pipelined():
-        for g in gnames:
-            grads[g].zero_()
+        st.wait_stream(stream)
+        with torch.cuda.stream(st):
+            for g in gnames:
+                grads[g].zero_()
         issue_copy(0)
-        for k in range(args.warmup):
-            step_pipelined(k, args.warmup - 1)
+        W_ = max(args.warmup, 2)
+        for k in range(W_):
+            step_pipelined(k, W_ - 1)
         torch.cuda.synchronize(dev)
         K = max(1, min(args.steps, 20))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(st)
         issue_copy(0)
         for k in range(K):
             step_pipelined(k, K - 1)
-        b.record(stream)
+        b.record(st)
         torch.cuda.synchronize(dev)
         return round(a.elapsed_time(b) / K, 4), K
 
@@ -565,8 +603,9 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
                 h2d_bytes_per_step=host_tgt.numel() * host_tgt.element_size(),
                 d2h_bytes_per_step=host_loss.numel() * host_loss.element_size(), steps=K,
                 inputs="target image up, loss down; scene parameters resident",
-                schedule="next target copied up during the step; the gradient rows the "
-                         "previous view wrote are zeroed (gs_zero_touched_gradients)",
+                schedule="one gs_render_batch_graph call per step; next target copied up "
+                         "during the step; the gradient rows the previous view wrote are zeroed "
+                         "(gs_zero_touched_gradients)",
                 serial=dict(value=v1, unit="ms/view",
                             schedule="copy up, zero all gradient rows, step, loss down, in one "
                                      "stream"),

@@ -15,6 +15,7 @@
  *                       per-splat reduction (Sec. 3.2, Procedure 2) and the chain
  *                       rule back to the 3D parameters
  *   gs_render_batch     a list of forward / forward+backward requests
+ *                       (gs_render_batch_graph: the same as one CUDA graph)
  *
  * Conventions
  *   - Every array pointer is CUDA device memory owned by the caller, row-major,
@@ -263,6 +264,23 @@ int gs_loss(const float* image, const float* target, int64_t n_values, int32_t k
  * largest).  Forward: project, sort, raster.  Forward+backward adds the loss
  * (if any) and the backward pass. */
 int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stream_t stream);
+
+/* gs_render_batch through a CUDA graph: the requests' ~20 launches per request
+ * are captured from `stream` into a graph and launched as one, without the
+ * gaps between dependent launches.  The executable graph is kept per workspace
+ * and updated in place when the next call has the same launch structure (new
+ * pointers, camera or counts are fine); otherwise it is rebuilt.  Same results
+ * and errors as gs_render_batch.  A request in the memory-efficiency mode
+ * (which reads its chunk count on the host), a legacy default stream (NULL,
+ * which cannot be captured) or a stream already being captured makes the call
+ * run as gs_render_batch.  Not thread-safe for one workspace (neither is any
+ * call on a workspace). */
+int gs_render_batch_graph(const gs_request* reqs, int32_t n, gs_workspace* ws,
+                          gs_stream_t stream);
+
+/* Frees the executable graph gs_render_batch_graph keeps for ws (if any).  Call
+ * before freeing a workspace's memory that will not be used again. */
+int gs_graph_release(gs_workspace* ws);
 
 /* Synchronises `stream` and returns the device status recorded in `ws`
  * (GS_OK, GS_ERR_CAPACITY or GS_ERR_TIMEOUT). */

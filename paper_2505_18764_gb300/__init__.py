@@ -183,6 +183,18 @@ class Workspace:
     def ref(self):
         return ctypes.byref(self.c)
 
+    def release_graph(self):
+        """Frees the CUDA graph render_batch(graph=True) keeps for this workspace."""
+        lib = _lib._lib
+        if lib is not None:
+            lib.gs_graph_release(ctypes.byref(self.c))
+
+    def __del__(self):
+        try:
+            self.release_graph()
+        except Exception:
+            pass
+
     @staticmethod
     def required_bytes(n_cap: int, width_cap: int, height_cap: int, opts: RasterOpts | None = None) -> int:
         nbytes = ctypes.c_size_t(0)
@@ -419,17 +431,22 @@ class Request:
     outputs: dict = field(default_factory=dict)
 
 
-def render_batch(requests, ws: Workspace, stream=None):
-    """Allocates each request's outputs, then runs all requests in one C call."""
+def render_batch(requests, ws: Workspace, stream=None, graph: bool = False):
+    """Allocates each request's outputs, then runs all requests in one C call
+    (`graph`: as one CUDA graph, gs_render_batch_graph; needs a non-default stream)."""
     lib = _lib.load()
     arr = (_lib.GsRequest * len(requests))()
     for i, rq in enumerate(requests):
         H, W = int(rq.camera.height), int(rq.camera.width)
         dev = ws.device
         out = rq.outputs
-        out.setdefault("image", torch.empty((H, W, 3), dtype=torch.float32, device=dev))
-        out.setdefault("state", alloc_state(H, W, rq.opts.state_format, dev))
-        out.setdefault("last", torch.empty((H, W), dtype=torch.int32, device=dev))
+        # outputs the caller did not provide are allocated (only then)
+        if "image" not in out:
+            out["image"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        if "state" not in out:
+            out["state"] = alloc_state(H, W, rq.opts.state_format, dev)
+        if "last" not in out:
+            out["last"] = torch.empty((H, W), dtype=torch.int32, device=dev)
         sc = rq.scene
         _check_scene(sc, rq.opts.sh_degree)
         _check_image_buffers(rq.camera, rq.opts.state_format, out["image"], out["state"], out["last"],
@@ -449,17 +466,25 @@ def render_batch(requests, ws: Workspace, stream=None):
             if rq.loss_kind:
                 c.loss_kind = {"l1": GS_LOSS_L1, "l2": GS_LOSS_L2}[rq.loss_kind]
                 c.target = _ptr(rq.target)
-                out.setdefault("dL_dimage", torch.empty((H, W, 3), dtype=torch.float32, device=dev))
-                out.setdefault("loss", torch.empty(1, dtype=torch.float64, device=dev))
+                if "dL_dimage" not in out:
+                    out["dL_dimage"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+                if "loss" not in out:
+                    out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
                 c.dL_dimage, c.loss = _ptr(out["dL_dimage"]), _ptr(out["loss"])
             else:
                 c.loss_kind = GS_LOSS_NONE
                 c.dL_dimage = _ptr(rq.dL_dimage)
-            g = out.setdefault("grads", zero_grads(sc))
+            if "grads" not in out:
+                out["grads"] = zero_grads(sc)
+            g = out["grads"]
             _check_grads(sc, g)
             c.d_means, c.d_scales, c.d_quats = _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"])
             c.d_opacities, c.d_sh = _ptr(g["opacities"]), _ptr(g["sh"])
-    check(lib.gs_render_batch(arr, len(requests), ws.ref, _stream(stream)), "gs_render_batch")
+    if graph:
+        check(lib.gs_render_batch_graph(arr, len(requests), ws.ref, _stream(stream)),
+              "gs_render_batch_graph")
+    else:
+        check(lib.gs_render_batch(arr, len(requests), ws.ref, _stream(stream)), "gs_render_batch")
     return requests
 
 

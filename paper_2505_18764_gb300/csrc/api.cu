@@ -3,7 +3,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -617,6 +619,75 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
       return fail(GS_ERR_INVALID_ARG, "request %d: bad mode %d", i, q.mode);
     }
     if (rc) return rc;
+  }
+  return GS_OK;
+}
+
+namespace {
+// Executable graphs of gs_render_batch_graph, one per workspace.
+std::mutex g_graph_mu;
+std::unordered_map<const gs_workspace*, cudaGraphExec_t> g_graphs;
+}  // namespace
+
+int gs_render_batch_graph(const gs_request* reqs, int32_t n, gs_workspace* ws,
+                          gs_stream_t stream) {
+  if (n < 0 || (n > 0 && !reqs)) return fail(GS_ERR_INVALID_ARG, "bad request list");
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  bool direct = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+  for (int i = 0; i < n && !direct; ++i) direct = reqs[i].opts.chunked != 0;
+  if (!direct) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GS_CUDA(cudaStreamIsCapturing(st, &cs), "capture status");
+    direct = cs != cudaStreamCaptureStatusNone;
+  }
+  if (!direct) {
+    // a workspace's first call runs directly: it sets up every launch's
+    // one-time host state (occupancy queries) outside any capture
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_graphs.find(ws) == g_graphs.end()) {
+      g_graphs[ws] = nullptr;
+      direct = true;
+    }
+  }
+  if (direct) return gs_render_batch(reqs, n, ws, stream);
+  GS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  rc = gs_render_batch(reqs, n, ws, stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (rc || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    return fail(GS_ERR_CUDA, "end capture: %s", cudaGetErrorString(ce));
+  }
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  cudaGraphExec_t& exec = g_graphs[ws];
+  if (exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();   // a failed update is not an error: rebuild
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (!exec) e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    exec = nullptr;
+    return fail(GS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  GS_CUDA(cudaGraphLaunch(exec, st), "graph launch");
+  return GS_OK;
+}
+
+int gs_graph_release(gs_workspace* ws) {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  auto it = g_graphs.find(ws);
+  if (it != g_graphs.end()) {
+    if (it->second) cudaGraphExecDestroy(it->second);
+    g_graphs.erase(it);
   }
   return GS_OK;
 }

@@ -452,6 +452,53 @@ def test_render_batch_matches_separate_calls():
         assert rel_l2(reqs[0].outputs["grads"][k].cpu().numpy(), grads[k].cpu().numpy()) < 1e-5
 
 
+def test_render_batch_graph_matches_direct():
+    """The graph form of render_batch gives the direct form's results on its
+    first call (run directly), its second (captured and instantiated), with a
+    new camera (updated in place), a new image size (rebuilt) and on the legacy
+    default stream (run directly)."""
+    scene_np, cam, target = syn.tiny_scene_1k()
+    opts = gs.RasterOpts()
+    scene = gs.SceneTensors.from_numpy(scene_np)
+    tt = torch.from_numpy(target).cuda()
+    cams = [cam, cam, syn.orbit_camera(1.0, 4.0, 60.0, cam.width, cam.height),
+            syn.orbit_camera(2.0, 4.0, 60.0, 96, 64)]
+    ws_g = gs.Workspace(scene.n, cam.width, cam.height, opts)
+    ws_d = gs.Workspace(scene.n, cam.width, cam.height, opts)
+    st = torch.cuda.Stream()
+
+    def reqs_for(c):
+        t = tt if (c.width, c.height) == (cam.width, cam.height) else \
+            torch.rand((c.height, c.width, 3), device="cuda")
+        return [gs.Request(scene, c, opts, backward=True, loss_kind="l1", target=t),
+                gs.Request(scene, cams[2], opts)]
+
+    for i, c in enumerate(cams + [cams[2]]):
+        legacy = i == len(cams)
+        rg, rd = reqs_for(c), None
+        rd = [gs.Request(q.scene, q.camera, q.opts, q.backward, q.loss_kind, q.target) for q in rg]
+        if legacy:
+            gs.render_batch(rg, ws_g, None, graph=True)
+        else:
+            st.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(st):
+                gs.render_batch(rg, ws_g, st, graph=True)
+            torch.cuda.current_stream().wait_stream(st)
+        gs.render_batch(rd, ws_d)
+        gs.check_status(ws_g)
+        gs.check_status(ws_d)
+        torch.cuda.synchronize()
+        for a, b in zip(rg, rd):
+            for key in ("image", "state", "last"):
+                assert torch.equal(a.outputs[key], b.outputs[key]), (i, key)
+        la, lb = rg[0].outputs["loss"].item(), rd[0].outputs["loss"].item()
+        assert abs(la - lb) <= 1e-9 * abs(lb), i
+        for k in GROUPS:
+            assert rel_l2(rg[0].outputs["grads"][k].cpu().numpy(),
+                          rd[0].outputs["grads"][k].cpu().numpy()) < 1e-5, (i, k)
+    ws_g.release_graph()
+
+
 @pytest.mark.parametrize("shape,offset", [((33, 47, 3), 0), ((33, 47, 3), 1), ((828, 1256, 3), 0)])
 def test_loss_kernel(shape, offset):
     """Aligned arrays take the float4 loop plus a scalar tail (33 x 47 x 3 is
