@@ -84,6 +84,15 @@ def test_workspace_size_and_argument_errors(lib):
     # calls on an uninitialised workspace are refused before any CUDA call
     assert lib.gs_sort(ctypes.byref(_lib.GsWorkspace()), None) == _lib.GS_ERR_INVALID_ARG
     assert lib.gs_loss(None, None, 10, 7, None, None, None) == _lib.GS_ERR_INVALID_ARG
+    blank = ctypes.byref(_lib.GsWorkspace())
+    assert lib.gs_zero_touched_gradients(blank, 0, None, None, None, None, None, None) == \
+        _lib.GS_ERR_INVALID_ARG
+    assert b"workspace" in lib.gs_last_error()
+    # the graph form of the batch call validates like the direct one, before any capture
+    assert lib.gs_render_batch_graph(None, 1, blank, None) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_render_batch_graph(None, -1, blank, None) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_render_batch_graph(None, 0, blank, None) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_graph_release(blank) == _lib.GS_OK   # nothing kept: a no-op
 
 
 def test_package_fails_loudly_without_library(tmp_path):
