@@ -16,13 +16,17 @@
  *                       rule back to the 3D parameters
  *   gs_render_batch     a list of forward / forward+backward requests
  *                       (gs_render_batch_graph: the same as one CUDA graph)
+ *   gs_zero_touched_gradients  zeroes the gradient rows the last view's backward
+ *                       added to (a training step's reset, proportional to V)
  *
  * Conventions
  *   - Every array pointer is CUDA device memory owned by the caller, row-major,
  *     float32 unless stated.  Host pointers are marked "host".
- *   - Calls are asynchronous on `stream` (a cudaStream_t) and never allocate:
- *     scratch lives in a caller-allocated workspace (gs_workspace_size /
- *     gs_workspace_init).  One workspace serves one stream at a time.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t) and never allocate
+ *     device memory: scratch lives in a caller-allocated workspace
+ *     (gs_workspace_size / gs_workspace_init).  One workspace serves one stream
+ *     at a time.  gs_render_batch_graph keeps one executable CUDA graph per
+ *     workspace (gs_graph_release frees it).
  *   - Parameters are activated values: scales > 0, opacities in [0, 1],
  *     quaternions (w, x, y, z) normalised inside, SH coefficients [N][K][3]
  *     with K = (sh_degree + 1)^2, real orthonormal basis with the
