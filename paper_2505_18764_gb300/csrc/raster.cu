@@ -124,6 +124,27 @@ __device__ __forceinline__ void lane_pixels(int x0, int y0, int lane, int& x, in
   own = COLS != 4 || lane < 16;
 }
 
+// The pixel-centre rectangle (x0, y0, wx, wy) of the warp's pixels still in
+// play (act_a: the lane's pixel (x, ya); act_b: (x, yb)): the forward tests a
+// group's candidates against it instead of the whole footprint, so once pixels
+// are T-culled the candidates that can only reach them are not walked (the
+// densest blocks, whose items end the launch, are T-culled almost everywhere).
+// At least one lane must have a pixel in play.  (In the backward, with pixels
+// past their last fragment, the same test cost more than it saved.)
+__device__ __forceinline__ void active_rect(bool act_a, bool act_b, int x, int ya, int yb,
+                                            float& x0, float& y0, float& wx, float& wy) {
+  const bool any = act_a || act_b;
+  const int lx = any ? x : 0x7fffffff, hx = any ? x : -1;
+  const int ly = act_a ? ya : (act_b ? yb : 0x7fffffff);
+  const int hy = act_b ? yb : (act_a ? ya : -1);
+  const int xmin = __reduce_min_sync(kFull, lx), xmax = __reduce_max_sync(kFull, hx);
+  const int ymin = __reduce_min_sync(kFull, ly), ymax = __reduce_max_sync(kFull, hy);
+  x0 = (float)xmin + 0.5f;
+  y0 = (float)ymin + 0.5f;
+  wx = (float)(xmax - xmin);
+  wy = (float)(ymax - ymin);
+}
+
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
@@ -207,9 +228,11 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
     __syncwarp();
     if (__all_sync(kFull, pa.done && pb.done)) break;
     const uint32_t cnt = min(32u, end - gs);
+    float rx, ry, rw, rh;
+    active_rect(!pa.done, NPX == 2 && !pb.done, x, ya, yb, rx, ry, rw, rh);
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
-                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
-                                                       (float)(COLS - 1), 3.f));
+                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], rx, ry,
+                                                       rw, rh));
     while (m) {
       const int j = __ffs(m) - 1;
       m &= m - 1u;
