@@ -69,8 +69,12 @@ enum {
  * kernels give each warp a footprint of 64 pixels (16x4) or, in blocks with
  * long splat lists, 32 (8x4) or 16 (4x4). */
 enum {
-  GS_REDUCE_WARP = 0, /* transpose-reduce over the warp: one vector-atomic triple per (splat, footprint) */
-  GS_REDUCE_NAIVE = 1 /* one vector-atomic triple per fragment (the paper's 1x baseline) */
+  GS_REDUCE_WARP = 0,    /* transpose-reduce over the warp: one vector-atomic triple per (splat,
+                            footprint) */
+  GS_REDUCE_NAIVE = 1,   /* one vector-atomic triple per lane that has a fragment (a lane's two
+                            pixels of a 16x4 band are added first) */
+  GS_REDUCE_FRAGMENT = 2 /* one vector-atomic triple per fragment, every pixel its own (the
+                            paper's 1x baseline of Sec. 4.3); front to back only */
 };
 
 /* Order in which the backward raster visits a pixel's fragments (Sec. 3.1.2).
@@ -352,15 +356,40 @@ int gs_sort_pairs(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* val
  * fixed array inside the library: every GPU that loads the library holds
  * about 4.3 MB for it until the process exits, and n may not exceed
  * GS_SORT_NOALLOC_MAX_PAIRS (larger n returns GS_ERR_INVALID_ARG with a
- * message).  It calls no allocator.  The first call on each device looks the
- * array up and zeroes it on `stream` before sorting, so make that first call
- * before any stream capture.  All calls on a device share the array, and it
- * keeps the last call's contents: calls that overlap on the GPU (on different
- * streams, or from different threads) race and corrupt each other; order them
- * on one stream or serialise them. */
+ * message).  It calls no allocator.  The array is used on the current device:
+ * keys_in must be memory of that device (else GS_ERR_INVALID_ARG).  Every call
+ * looks the array's address up again; the first call on each device (and the
+ * first after cudaDeviceReset moved the array) zeroes it on `stream` before
+ * sorting, so make that first call before any stream capture.  All calls on a
+ * device share the array, and it keeps the last call's contents: calls that
+ * overlap on the GPU (on different streams, or from different threads) race
+ * and corrupt each other; order them on one stream or serialise them.  A wait
+ * on the device that gave up (GS_ERR_TIMEOUT, a wrong result) is reported by
+ * gs_sort_pairs_noalloc_status, not by the call itself. */
 #define GS_SORT_NOALLOC_MAX_PAIRS 262144
 int gs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                           uint32_t* vals_out, int32_t n, int32_t key_bits, gs_stream_t stream);
+
+/* Device status of the last gs_sort_pairs_noalloc on the current device:
+ * synchronises `stream` (the stream of that call) and returns GS_OK, or
+ * GS_ERR_TIMEOUT when one of its look-back waits gave up (its output is then
+ * wrong).  The next gs_sort_pairs_noalloc on the device clears the status, so
+ * read it before that call.  Allocates nothing; GS_OK before any call. */
+int gs_sort_pairs_noalloc_status(gs_stream_t stream);
+
+/* Self-test of the bounded device waits (a testing aid, not part of the
+ * paper's method).  Runs the first radix pass of gs_sort_pairs (ws != NULL,
+ * n <= ws->n_cap) or of gs_sort_pairs_noalloc (ws == NULL, n <=
+ * GS_SORT_NOALLOC_MAX_PAIRS) on n > 2048 keys (at least two tiles) with tile 0
+ * withheld: no CTA ever publishes tile 0's look-back word, so every wait on it
+ * gives up after `spin_limit` polls (1 .. 2^22; ~1e4 polls take a few
+ * milliseconds).  The pass then finishes with a wrong result written inside
+ * keys_out / vals_out (n entries each) and records GS_ERR_TIMEOUT, which
+ * gs_check_status(ws) or gs_sort_pairs_noalloc_status returns; the kernel
+ * returns and the CUDA context stays usable. */
+int gs_test_stalled_sort(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* vals_in,
+                         uint32_t* keys_out, uint32_t* vals_out, int32_t n, uint32_t spin_limit,
+                         gs_stream_t stream);
 
 #ifdef __cplusplus
 }

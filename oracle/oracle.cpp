@@ -788,6 +788,26 @@ int oracle_splat_grads(int N, const double* means, const double* scales, const d
     }
     const int w = std::max(0, x1 - x0 + 1), h = std::max(0, y1 - y0 + 1);
     pixel_count[j] = w * h;
+    // The splats (in depth order) that can reach a pixel of this rectangle.  A
+    // splat has alpha >= 1/255 only inside the ellipse d^T Q d <= 2 ln(255 o)
+    // (and its tie band only inside d^T Q d <= 2 (ln(255 o) + band_cut)); one
+    // whose box of the wider ellipse, grown by a pixel, misses the rectangle's
+    // pixel centres adds nothing there, so tracing the rest gives the same
+    // fragment lists as tracing every splat.
+    std::vector<int> sub;
+    if (w > 0 && h > 0) {
+      const double rx0 = x0 + 0.5, rx1 = x1 + 0.5, ry0 = y0 + 0.5, ry1 = y1 + 0.5;
+      for (int id2 : ord) {
+        const Splat& t = sp[id2];
+        const double kk = 2.0 * (std::log(255.0 * t.opacity) + op.band_cut);
+        if (!(t.opacity > 0.0) || !(kk >= 0.0)) continue;
+        const double ex2 = std::sqrt(kk * t.S2[0][0]) + 1.0, ey2 = std::sqrt(kk * t.S2[1][1]) + 1.0;
+        if (t.mu2[0] + ex2 < rx0 || t.mu2[0] - ex2 > rx1 || t.mu2[1] + ey2 < ry0 ||
+            t.mu2[1] - ey2 > ry1)
+          continue;
+        sub.push_back(id2);
+      }
+    }
     const int nt = num_threads();
     std::vector<double> part(static_cast<size_t>(nt) * kG2, 0.0);
 #pragma omp parallel
@@ -798,7 +818,7 @@ int oracle_splat_grads(int N, const double* means, const double* scales, const d
       for (int p = 0; p < w * h; ++p) {
         const int px = x0 + p % w, py = y0 + p / w;
         PixelResult r;
-        trace_pixel(px, py, sp, ord, cam, op, &fr, r);
+        trace_pixel(px, py, sp, sub, cam, op, &fr, r);
         const int n = static_cast<int>(fr.size());
         // suffix sums over the whole fragment list, then keep the selected splat
         std::vector<double> S((n + 1) * 3, 0.0);

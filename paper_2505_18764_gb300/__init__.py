@@ -17,7 +17,7 @@ from ._lib import (GS_LOSS_L1, GS_LOSS_L2, GS_LOSS_NONE, GS_MODE_FORWARD, GS_MOD
 
 STATE_FORMATS = {"fp32": 0, "fp16": 1, "unorm16": 2, "unorm8": 3}
 STATE_BYTES = {"fp32": 16, "fp16": 8, "unorm16": 8, "unorm8": 4}
-REDUCE_MODES = {"warp": 0, "naive": 1}
+REDUCE_MODES = {"warp": 0, "naive": 1, "fragment": 2}
 BACKWARD_ORDERS = {"front_to_back": 0, "back_to_front": 1}
 NONE_RANK = 0xFFFFFFFF
 
@@ -411,10 +411,37 @@ def sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 3
     GS_SORT_NOALLOC_MAX_PAIRS pairs; calls overlapping on the GPU race)."""
     if keys.dtype != torch.int32 or vals.dtype != torch.int32 or keys.numel() != vals.numel():
         raise ValueError("keys and vals must be int32 tensors of the same size")
+    if keys.device != vals.device:
+        raise ValueError("keys and vals must be on the same device")
     ko, vo = torch.empty_like(keys), torch.empty_like(vals)
-    check(_lib.load().gs_sort_pairs_noalloc(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo),
-                                            keys.numel(), key_bits, _stream(stream)),
-          "gs_sort_pairs_noalloc")
+    with torch.cuda.device(keys.device):   # the library uses the current device's array
+        check(_lib.load().gs_sort_pairs_noalloc(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo),
+                                                keys.numel(), key_bits, _stream(stream)),
+              "gs_sort_pairs_noalloc")
+    return ko, vo
+
+
+def sort_pairs_noalloc_status(device=None, stream=None):
+    """Raises GsError(GS_ERR_TIMEOUT) when a look-back wait of the last
+    sort_pairs_noalloc on `device` gave up (synchronises the stream)."""
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        check(_lib.load().gs_sort_pairs_noalloc_status(_stream(stream)),
+              "gs_sort_pairs_noalloc_status")
+
+
+def stalled_sort_selftest(ws, keys: torch.Tensor, vals: torch.Tensor, spin_limit: int, stream=None):
+    """Self-test of the bounded device waits: one radix pass with tile 0
+    withheld, so its look-back waits give up after `spin_limit` polls and the
+    device status reads GS_ERR_TIMEOUT.  ws None: the allocation-free sort's
+    array.  Returns the (wrong) output tensors."""
+    if keys.dtype != torch.int32 or vals.dtype != torch.int32 or keys.numel() != vals.numel():
+        raise ValueError("keys and vals must be int32 tensors of the same size")
+    ko, vo = torch.empty_like(keys), torch.empty_like(vals)
+    with torch.cuda.device(keys.device):
+        check(_lib.load().gs_test_stalled_sort(ws.ref if ws is not None else None, _ptr(keys),
+                                               _ptr(vals), _ptr(ko), _ptr(vo), keys.numel(),
+                                               int(spin_limit), _stream(stream)),
+              "gs_test_stalled_sort")
     return ko, vo
 
 
@@ -491,5 +518,5 @@ def render_batch(requests, ws: Workspace, stream=None, graph: bool = False):
 __all__ = ["RasterOpts", "SceneTensors", "Workspace", "project", "sort", "raster_forward", "bin",
            "blend_forward", "blend_backward", "project_backward",
            "raster_backward", "loss", "render", "render_batch", "Request", "check_status",
-           "read_counters", "fp32_fma_rate", "copy_array", "sort_pairs", "sort_pairs_noalloc", "decode_state", "alloc_state",
+           "read_counters", "fp32_fma_rate", "copy_array", "sort_pairs", "sort_pairs_noalloc", "sort_pairs_noalloc_status", "stalled_sort_selftest", "decode_state", "alloc_state",
            "camera_to_c", "GsError", "zero_grads", "NONE_RANK"]

@@ -21,7 +21,7 @@ GS_ERR_TIMEOUT = -3
 GS_ERR_CUDA = -4
 
 GS_STATE_FP32, GS_STATE_FP16, GS_STATE_UNORM16, GS_STATE_UNORM8 = 0, 1, 2, 3
-GS_REDUCE_WARP, GS_REDUCE_NAIVE = 0, 1
+GS_REDUCE_WARP, GS_REDUCE_NAIVE, GS_REDUCE_FRAGMENT = 0, 1, 2
 GS_SPLIT_THRESHOLD_DEFAULT = 1536
 GS_REDUCE_THRESHOLD_DEFAULT = 16
 GS_BWD_FRONT_TO_BACK, GS_BWD_BACK_TO_FRONT = 0, 1
@@ -97,6 +97,9 @@ _SIGS = {
     "gs_sort_pairs": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                       c_int32, c_void_p],
     "gs_sort_pairs_noalloc": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p],
+    "gs_sort_pairs_noalloc_status": [c_void_p],
+    "gs_test_stalled_sort": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                             c_uint32, c_void_p],
     "gs_fp32_fma_rate": [c_int32, POINTER(c_double), c_void_p],
     "gs_zero_touched_gradients": [POINTER(GsWorkspace), c_int32, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p],

@@ -25,7 +25,11 @@ cudaError_t launch_zero_touched(int, int, const uint32_t*, const Header*, float*
 cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,
                                  const uint32_t*, uint32_t, uint32_t, uint32_t, int, uint32_t,
                                  const uint32_t*, unsigned long long*, uint32_t*, const uint32_t*,
-                                 uint32_t, uint32_t*, int, int, cudaStream_t);
+                                 uint32_t, uint32_t*, int, int, cudaStream_t,
+                                 uint32_t spin_limit = kSpinLimit);
+cudaError_t launch_set_word(uint32_t*, uint32_t, cudaStream_t);
+int noalloc_stalled_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int32_t,
+                         uint32_t, cudaStream_t);
 cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
 cudaError_t launch_bin_count(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*,
@@ -162,7 +166,9 @@ T* at(const gs_workspace* ws, int slot) {
 int check_opts(const gs_raster_opts* o) {
   if (!o) return fail(GS_ERR_INVALID_ARG, "opts is null");
   if (o->state_format < 0 || o->state_format > 3) return fail(GS_ERR_INVALID_ARG, "bad state_format %d", o->state_format);
-  if (o->reduce_mode < 0 || o->reduce_mode > 1) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
+  if (o->reduce_mode < 0 || o->reduce_mode > 2) return fail(GS_ERR_INVALID_ARG, "bad reduce_mode %d", o->reduce_mode);
+  if (o->reduce_mode == GS_REDUCE_FRAGMENT && o->backward_order != GS_BWD_FRONT_TO_BACK)
+    return fail(GS_ERR_INVALID_ARG, "GS_REDUCE_FRAGMENT walks front to back only");
   if (o->split_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad split_threshold %d", o->split_threshold);
   if (o->reduce_threshold < 0) return fail(GS_ERR_INVALID_ARG, "bad reduce_threshold %d", o->reduce_threshold);
   if (o->backward_order < 0 || o->backward_order > 1)
@@ -784,6 +790,33 @@ int gs_sort_pairs(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* val
                                  grid_cap, st),
             "sort pass");
   }
+  return GS_OK;
+}
+
+int gs_test_stalled_sort(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* vals_in,
+                         uint32_t* keys_out, uint32_t* vals_out, int32_t n, uint32_t spin_limit,
+                         gs_stream_t stream) {
+  if (spin_limit < 1 || spin_limit > kSpinLimit)
+    return fail(GS_ERR_INVALID_ARG, "spin_limit must be in [1, %u]", kSpinLimit);
+  if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(GS_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!ws) return noalloc_stalled_pass(keys_in, vals_in, keys_out, vals_out, n, spin_limit, st);
+  int rc = check_ws(ws);
+  if (rc) return rc;
+  if (n <= 2048) return fail(GS_ERR_INVALID_ARG, "n must span at least two sort tiles (> 2048)");
+  if (n > ws->n_cap) return fail(GS_ERR_INVALID_ARG, "n = %d exceeds the capacity %d", n, ws->n_cap);
+  Header* hdr = at<Header>(ws, L_HDR);
+  uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
+  GS_CUDA(cudaMemsetAsync(hdr, 0, sizeof(Header), st), "sort memset");
+  GS_CUDA(launch_bump_epoch(epoch, st), "epoch kernel");
+  GS_CUDA(launch_digit_hist(keys_in, (uint32_t)n, 1, &hdr->depth_hist[0][0], num_sms(), st), "histogram kernel");
+  // tile 0 withheld: CTAs take tiles from 1 on, so no CTA publishes tile 0
+  GS_CUDA(launch_set_word(&hdr->tile_counter[9], 1u, st), "tile counter");
+  GS_CUDA(launch_onesweep_pass(keys_in, vals_in, keys_out, vals_out, nullptr, (uint32_t)n,
+                               (uint32_t)n, (uint32_t)n, 0, 0xFFu, hdr->depth_hist[0],
+                               at<unsigned long long>(ws, L_STATUS), &hdr->tile_counter[9], epoch,
+                               8u, &hdr->status, 0, num_sms() * kPersistentPerSm, st, spin_limit),
+          "stalled sort pass");
   return GS_OK;
 }
 

@@ -416,6 +416,85 @@ __device__ __forceinline__ void red_add9(float* dst, const float v[9]) {
   red_add_v4(dst + 8, v[8], 0.f, 0.f, 0.f);
 }
 
+// ---------------------------------------------------------------------------
+// The two pixels of a lane in a 16x4 band, (x, ya) and (x, ya + 2), walked as
+// packed FP32 pairs: each operation below is one FP32x2 instruction that
+// rounds both halves exactly as the scalar operation does, so a candidate
+// costs about half the issue slots of two scalar walks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// q at both pixels, bit-identical to frag_q2 (dx and y1 are common).
+__device__ __forceinline__ float2 frag_q_pair(float px, float2 py, const float4& a,
+                                              const float4& b, float& y1, float2& y2) {
+  const float dx = __fsub_rn(__fsub_rn(px, a.x), b.z);
+  const float2 dy = __fadd2_rn(__fadd2_rn(py, f2(-a.y)), f2(-b.w));   // x - y == x + (-y)
+  y1 = __fmul_rn(a.z, dx);
+  y2 = __fmul2_rn(f2(b.x), __ffma2_rn(f2(-a.w), f2(dx), dy));
+  return __ffma2_rn(f2(y1), f2(y1), __fmul2_rn(y2, y2));
+}
+
+struct PairBwd {
+  float2 nC0, nC1, nC2;   // -C' of the two pixels (Eq. 6 then adds T alpha c)
+  float2 T, g0, g1, g2;
+  uint32_t end_a, end_b;  // depth rank after each pixel's last fragment
+};
+
+__device__ __forceinline__ PairBwd pack_pair(const PixelBwd& a, const PixelBwd& b) {
+  PairBwd p;
+  p.nC0 = make_float2(-a.Cp0, -b.Cp0);
+  p.nC1 = make_float2(-a.Cp1, -b.Cp1);
+  p.nC2 = make_float2(-a.Cp2, -b.Cp2);
+  p.T = make_float2(a.T, b.T);
+  p.g0 = make_float2(a.g0, b.g0);
+  p.g1 = make_float2(a.g1, b.g1);
+  p.g2 = make_float2(a.g2, b.g2);
+  p.end_a = a.end;
+  p.end_b = b.end;
+  return p;
+}
+
+// One candidate of Procedure 1 at both pixels of a lane, as grad_fragment:
+// a missed pixel runs with G = 0, which leaves its state unchanged and gives
+// exact zeros.  t[k] holds the two pixels' contributions to value k.
+__device__ __forceinline__ void grad_pair(PairBwd& p, bool ha, bool hb, float2 q, float y1,
+                                          float2 y2, const float4& a, const float4& b,
+                                          const float4& c, float2 t[9]) {
+  const float2 G = make_float2(ha ? ex2_approx(-q.x) : 0.0f, hb ? ex2_approx(-q.y) : 0.0f);
+  const float2 at = __fmul2_rn(f2(c.w), G);
+  const float2 alpha = make_float2(fminf(kAlphaMax, at.x), fminf(kAlphaMax, at.y));
+  const float2 oma = __ffma2_rn(alpha, f2(-1.0f), f2(1.0f));   // 1 - alpha, rounded once
+  const float2 wT = __fmul2_rn(alpha, p.T);
+  // Eq. 3
+  t[5] = __fmul2_rn(p.g0, wT);
+  t[6] = __fmul2_rn(p.g1, wT);
+  t[7] = __fmul2_rn(p.g2, wT);
+  // Eq. 7 with C'_i before its update: g . (c T - C') / (1 - alpha)
+  const float2 e0 = __ffma2_rn(f2(c.x), p.T, p.nC0);
+  const float2 e1 = __ffma2_rn(f2(c.y), p.T, p.nC1);
+  const float2 e2 = __ffma2_rn(f2(c.z), p.T, p.nC2);
+  const float2 gs = __ffma2_rn(p.g0, e0, __ffma2_rn(p.g1, e1, __fmul2_rn(p.g2, e2)));
+  const float2 dLda =
+      __fmul2_rn(gs, make_float2(__fdividef(1.0f, oma.x), __fdividef(1.0f, oma.y)));
+  // Eq. 6, Eq. 5
+  p.nC0 = __ffma2_rn(wT, f2(c.x), p.nC0);
+  p.nC1 = __ffma2_rn(wT, f2(c.y), p.nC1);
+  p.nC2 = __ffma2_rn(wT, f2(c.z), p.nC2);
+  p.T = __fmul2_rn(p.T, oma);
+  // alpha = min(0.99, o G): no gradient through the clamp
+  const float2 d_at = make_float2(at.x < kAlphaMax ? dLda.x : 0.0f, at.y < kAlphaMax ? dLda.y : 0.0f);
+  t[8] = __fmul2_rn(G, d_at);
+  // z = Sigma^-1 d (see grad_fragment), weighted by dL/dpower
+  const float2 w = __fmul2_rn(at, d_at);
+  const float2 z1 = __fmul2_rn(f2(b.x), y2);
+  const float2 z0 = __ffma2_rn(f2(-a.w), z1, f2(a.z * y1));
+  t[0] = __fmul2_rn(w, z0);
+  t[1] = __fmul2_rn(w, z1);
+  t[2] = __fmul2_rn(t[0], z0);
+  t[3] = __fmul2_rn(t[0], z1);
+  t[4] = __fmul2_rn(t[1], z1);
+}
+
 // Candidate j's nine values v of this lane (frag: the lane had a fragment):
 // added directly when fewer than `threshold` lanes have one (Sec. 3.2.4),
 // else summed over the warp into part[j] and marked in `reduced`.
@@ -423,7 +502,7 @@ template <int MODE>
 __device__ __forceinline__ void reduce_candidate(const float v[9], bool frag, int j, uint32_t rank,
                                                  float (*part)[12], float* g2d, int threshold,
                                                  int tslot, int lane, uint32_t& reduced) {
-  if (MODE == GS_REDUCE_NAIVE) {
+  if (MODE != GS_REDUCE_WARP) {
     if (frag) red_add9(g2d + (size_t)rank * 12, v);
   } else {
     const uint32_t active = __ballot_sync(kFull, frag);
@@ -444,7 +523,7 @@ __device__ __forceinline__ void reduce_candidate(const float v[9], bool frag, in
 template <int MODE>
 __device__ __forceinline__ void flush_reduced(float (*part)[12], const WarpRing& R, int slot,
                                               uint32_t reduced, float* g2d, int lane) {
-  if (MODE == GS_REDUCE_NAIVE || !reduced) return;
+  if (MODE != GS_REDUCE_WARP || !reduced) return;
   __syncwarp();
   if ((reduced >> lane) & 1u) {
     const float4* p = reinterpret_cast<const float4*>(part[lane]);
@@ -530,6 +609,94 @@ __device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
   if (chunk_out) {
     if (va) chunk_state[(size_t)ya * W + x] = make_float4(pa.Cp0, pa.Cp1, pa.Cp2, pa.T);
     if (vb) chunk_state[(size_t)yb * W + x] = make_float4(pb.Cp0, pb.Cp1, pb.Cp2, pb.T);
+  }
+}
+
+// The 16x4 band (two pixels per lane) of bwd_item with the pixel pair packed
+// (grad_pair); in GS_REDUCE_FRAGMENT mode each pixel's fragment adds its own
+// values to the splat's accumulators.
+template <int MODE>
+__device__ __forceinline__ void bwd_item_pair(WarpRing& R, float (*part)[12],
+                                              const SplatRec* __restrict__ rec,
+                                              const uint32_t* __restrict__ pair_ranks,
+                                              uint2 range, int x0, int y0, int lane, int W,
+                                              int H, int fmt, const void* state,
+                                              const uint32_t* last_in, const float* dLdC,
+                                              float* g2d, int threshold, float4* chunk_state,
+                                              int chunk_in, int chunk_out) {
+  int x, ya;
+  bool own;
+  lane_pixels<16>(x0, y0, lane, x, ya, own);
+  const int yb = ya + 2;
+  const float px = (float)x + 0.5f;
+  const float2 py = make_float2((float)ya + 0.5f, (float)yb + 0.5f);
+  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
+  const int tslot = transpose_slot(lane);
+  const bool va = x < W && ya < H, vb = x < W && yb < H;
+  PairBwd pp;
+  {
+    PixelBwd pa, pb;
+    load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
+    load_pixel_bwd(pb, vb, x, yb, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
+    pp = pack_pair(pa, pb);
+  }
+  // depth ranks >= this contribute nowhere in the footprint
+  const uint32_t warp_end = __reduce_max_sync(kFull, max(pp.end_a, pp.end_b));
+
+  const uint32_t beg = range.x, end = warp_end > 0u ? range.y : range.x;
+  if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
+  int slot = 0;
+  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kStages - 1)) {
+    const uint32_t ip = gs + 32u * kStages + lane;
+    const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
+    cp_async_wait_group<kStages - 1>();
+    __syncwarp();
+    if (R.rank[slot][0] >= warp_end) break;   // ranks ascend along the list
+    const uint32_t cnt = min(32u, end - gs);
+    uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
+                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
+                                                       15.f, 3.f));
+    uint32_t reduced = 0u;   // candidates whose warp sums wait in `part`
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const uint32_t rank = R.rank[slot][j];
+      const float4 a = R.a[slot][j];
+      const float4 b = R.b[slot][j];
+      float y1;
+      float2 y2;
+      const float2 q = frag_q_pair(px, py, a, b, y1, y2);
+      const bool ha = rank < pp.end_a && q.x <= b.y;
+      const bool hb = rank < pp.end_b && q.y <= b.y;
+      if (!__any_sync(kFull, ha || hb)) continue;
+      const float4 c = R.c[slot][j];
+      float2 t[9];
+      grad_pair(pp, ha, hb, q, y1, y2, a, b, c, t);
+      if (MODE == GS_REDUCE_FRAGMENT) {
+        float va9[9], vb9[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          va9[k] = t[k].x;
+          vb9[k] = t[k].y;
+        }
+        if (ha) red_add9(g2d + (size_t)rank * 12, va9);
+        if (hb) red_add9(g2d + (size_t)rank * 12, vb9);
+      } else {
+        float v[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) v[k] = t[k].x + t[k].y;
+        reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
+      }
+    }
+    flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
+    __syncwarp();   // every lane is done with the slot and `part` before they are reused
+    ring_issue(R, slot, rec, ip, end, rk_next, lane);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  if (chunk_out) {
+    if (va) chunk_state[(size_t)ya * W + x] = make_float4(-pp.nC0.x, -pp.nC1.x, -pp.nC2.x, pp.T.x);
+    if (vb) chunk_state[(size_t)yb * W + x] = make_float4(-pp.nC0.y, -pp.nC1.y, -pp.nC2.y, pp.T.y);
   }
 }
 
@@ -748,8 +915,8 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
       continue;
     }
     if (cols == 16)
-      bwd_item<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                         last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
+      bwd_item_pair<MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+                          last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
     else if (cols == 8)
       bwd_item<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                         last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
@@ -869,6 +1036,12 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_NAIVE>);
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_NAIVE><<<grid, kThreads, 0, st>>>(
+        ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
+        threshold, back, chunk_state, chunk_in, chunk_out);
+  } else if (mode == GS_REDUCE_FRAGMENT) {
+    static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_FRAGMENT>);
+    const int grid = per_sm * num_sms;
+    raster_bwd_kernel<GS_REDUCE_FRAGMENT><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
         threshold, back, chunk_state, chunk_in, chunk_out);
   } else {

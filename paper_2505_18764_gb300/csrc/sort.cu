@@ -10,9 +10,10 @@
 //
 // Look-back status words are 64-bit: [63:32] tag (epoch * 16 + pass, so words
 // of earlier passes or views never match), [31:30] flag (1 = tile aggregate,
-// 2 = inclusive prefix), [29:0] count.  Waits are bounded: after kSpinLimit
-// polls a CTA records kStatusTimeout and continues (positions it writes then
-// stay inside the output; the result is wrong but nothing hangs).
+// 2 = inclusive prefix), [29:0] count.  Waits are bounded: after spin_limit
+// polls (kSpinLimit in every pass the library runs for its callers) a CTA
+// records kStatusTimeout and continues (positions it writes then stay inside
+// the output; the result is wrong but nothing hangs).
 #include "common.cuh"
 
 namespace gsr {
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     const uint32_t* __restrict__ n_dev, uint32_t n_static, uint32_t out_cap, int shift,
     uint32_t mask, const uint32_t* __restrict__ hist, unsigned long long* __restrict__ status,
     uint32_t* __restrict__ tile_counter, const uint32_t* __restrict__ epoch, uint32_t pass_id,
-    uint32_t* __restrict__ status_word, int drop_sentinel) {
+    uint32_t* __restrict__ status_word, int drop_sentinel, uint32_t spin_limit) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wcnt[kSortWarps][256];
   __shared__ uint32_t s_gbase[256];
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
         found = (w[i] & (3ull << 30)) == kFlagPre;
       }
       if (used == 0) {
-        if (++spins > kSpinLimit) {
+        if (++spins > spin_limit) {
           atomicOr(status_word, kStatusTimeout);
           break;
         }
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(256) digit_hist_kernel(const uint32_t* __restr
 }
 
 __global__ void bump_epoch_kernel(uint32_t* epoch) { *epoch += 1u; }
+__global__ void set_word_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
 cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in,
                                  uint32_t* keys_out, uint32_t* vals_out, const uint32_t* n_dev,
@@ -217,13 +219,13 @@ cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_i
                                  uint32_t mask, const uint32_t* hist, unsigned long long* status,
                                  uint32_t* tile_counter, const uint32_t* epoch, uint32_t pass_id,
                                  uint32_t* status_word, int drop_sentinel, int grid_cap,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, uint32_t spin_limit) {
   uint32_t tiles = (n_cap + kSortTile - 1) / kSortTile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > (uint32_t)grid_cap) tiles = (uint32_t)grid_cap;
   onesweep_pass_kernel<<<tiles, kSortThreads, 0, st>>>(
       keys_in, vals_in, keys_out, vals_out, n_dev, n_static, out_cap, shift, mask, hist, status,
-      tile_counter, epoch, pass_id, status_word, drop_sentinel);
+      tile_counter, epoch, pass_id, status_word, drop_sentinel, spin_limit);
   return cudaGetLastError();
 }
 
@@ -238,6 +240,11 @@ cudaError_t launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, uint
 
 cudaError_t launch_bump_epoch(uint32_t* epoch, cudaStream_t st) {
   bump_epoch_kernel<<<1, 1, 0, st>>>(epoch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_word(uint32_t* p, uint32_t v, cudaStream_t st) {
+  set_word_kernel<<<1, 1, 0, st>>>(p, v);
   return cudaGetLastError();
 }
 

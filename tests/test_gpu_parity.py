@@ -389,7 +389,8 @@ def test_zero_touched_gradients(deg):
         assert rel_l2(a.astype(np.float64), b.astype(np.float64)) < 1e-5, k
 
 
-@pytest.mark.parametrize("mode,thr", [("naive", 0), ("warp", 8), ("warp", 33), ("warp", 1)])
+@pytest.mark.parametrize("mode,thr", [("naive", 0), ("fragment", 0), ("warp", 8), ("warp", 33),
+                                      ("warp", 1)])
 def test_reduction_modes_agree(mode, thr):
     """The reduction is exactly a sum: every mode gives the same per-splat
     accumulators up to FP32 reassociation."""
@@ -584,7 +585,7 @@ def test_footprints_give_identical_images(which):
 
 
 @pytest.mark.parametrize("split", [1, 48, 1 << 30])
-@pytest.mark.parametrize("mode", ["warp", "naive"])
+@pytest.mark.parametrize("mode", ["warp", "naive", "fragment"])
 def test_footprints_backward_match_oracle(split, mode):
     scene_np, cam = _split_scenes()[0]
     g = syn.uniform_image(cam.height, cam.width, seed=74, lo=-1.0, hi=1.0)

@@ -454,16 +454,95 @@ def test_selected_splat_gradients_match_full_backward():
         np.testing.assert_allclose(sel[k], full[k][ids], rtol=1e-9, atol=1e-12)
 
 
-def test_fp16_cprime_emulation_changes_little():
-    scene, cam, _ = syn.tiny_scene_1k()
-    g = syn.uniform_image(cam.height, cam.width, seed=15, lo=-1.0, hi=1.0)
-    ex = oracle.backward(scene, cam, g, oracle.opts_array())
-    q = oracle.backward(scene, cam, g, oracle.opts_array(quant=1), quant_cprime=True)
-    for k in ("means", "opacities"):
-        err = np.linalg.norm(q[k] - ex[k]) / np.linalg.norm(ex[k])
-        assert 0 < err < 5e-2
-    # colour gradients do not depend on C'
-    np.testing.assert_allclose(q["sh"], ex["sh"], rtol=1e-12, atol=1e-12)
+def _quantize_numpy(x, fmt):
+    """Reduced-precision round trip by library routines: numpy's float16
+    conversion (round to nearest even), or unorm with numpy's half-to-even round."""
+    x = np.asarray(x, dtype=np.float64)
+    if fmt == "fp16":
+        return x.astype(np.float16).astype(np.float64)
+    s = 65535.0 if fmt == "unorm16" else 255.0
+    return np.round(np.clip(x, 0.0, 1.0) * s) / s
+
+
+def test_cprime_from_rounded_state_matches_closed_form():
+    """The backward's C'_1 taken from a reduced-precision stored colour (Sec. 3.3):
+    for one splat every pixel holds one fragment with T = 1, so Eq. 7 gives
+    dL/dalpha = g . (c - round(C)) / (1 - alpha) against g . c when C'_1 = C; the
+    opacity accumulator therefore moves by sum_p G_p g_p . (C_p - round(C_p)) /
+    (1 - alpha_p), with C_p, alpha_p = 1 - T_p from the (pinned) forward and the
+    rounding by numpy.  Colour gradients (Eq. 3) do not involve C'."""
+    W = H = 24
+    cam = syn.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 40.0, W, H)
+    sc = _one_splat((0.05, -0.03, 0.0), (0.3, 0.22, 0.26), (0.9, 0.1, -0.2, 0.3), 0.7,
+                    (0.83, 0.41, 0.17))
+    g = syn.uniform_image(H, W, seed=15, lo=-1.0, hi=1.0).astype(np.float64)
+    for fmt in ("fp16", "unorm8"):
+        ex = oracle.backward(sc, cam, g, oracle.opts_array(t_cull=0.0, clamp01=True))
+        q = oracle.backward(sc, cam, g, oracle.opts_array(t_cull=0.0, clamp01=True,
+                                                          quant=oracle.QUANT[fmt]),
+                            quant_cprime=True)
+        r = oracle.render(sc, cam, oracle.opts_array(t_cull=0.0, clamp01=True))
+        C, T, nf = r["color"], r["T"], r["nfrag"]
+        alpha = 1.0 - T
+        o = float(sc.opacities[0])
+        m = (nf == 1) & (alpha < 0.99)
+        delta = np.sum(g * (C - _quantize_numpy(C, fmt)), axis=2)   # g . (C - round(C))
+        expect = np.sum((alpha[m] / o) * delta[m] / (1.0 - alpha[m]))
+        got = q["g2d"][0, 8] - ex["g2d"][0, 8]
+        assert abs(expect) > 1e-6
+        assert abs(got - expect) <= 1e-9 * max(1.0, abs(expect)), (fmt, got, expect)
+        np.testing.assert_allclose(q["g2d"][0, 5:8], ex["g2d"][0, 5:8], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(q["sh"], ex["sh"], rtol=1e-12, atol=1e-15)
+
+
+def _three_fragment_pixel():
+    """Three splats straddling the optical axis at increasing depth; the pixel
+    at the image centre holds one fragment of each (opacities chosen so that
+    every alpha lies in (1/255, 0.99))."""
+    sh = np.zeros((3, 1, 3), np.float32)
+    rgbs = ((0.9, 0.2, 0.35), (0.15, 0.75, 0.6), (0.55, 0.45, 0.95))
+    for i, rgb in enumerate(rgbs):
+        sh[i, 0] = (np.array(rgb) - 0.5) / Y00
+    sc = syn.Scene(np.array([[0.01, 0.02, -1.0], [-0.03, 0.0, 0.0], [0.02, -0.01, 1.0]], np.float32),
+                   np.array([[0.4, 0.35, 0.3], [0.5, 0.5, 0.45], [0.6, 0.55, 0.6]], np.float32),
+                   np.array([[1, 0, 0, 0], [0.9, 0.2, 0.1, 0.0], [0.8, 0.0, 0.3, 0.2]], np.float32),
+                   np.array([0.55, 0.6, 0.85], np.float32), sh, 0)
+    cam = syn.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 40.0, 9, 9)
+    return sc, cam, 4 * 9 + 4
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "unorm16", "unorm8"])
+def test_per_fragment_rounding_matches_a_hand_loop(fmt):
+    """The paper's render-target round trip (Sec. 3.3): with per-fragment
+    rounding the state (C, T) is rounded after every blend.  A hand-written
+    loop over the three fragments of one pixel, taking the splats' projected
+    alpha and colour from the oracle's projection and rounding with numpy,
+    gives the same colour and transmittance; store-only rounding differs."""
+    sc, cam, pix = _three_fragment_pixel()
+    P = oracle.project(sc, cam, clamp01=True)
+    px, py = pix % cam.width + 0.5, pix // cam.width + 0.5
+    C, T = np.zeros(3), 1.0
+    for i in np.argsort(P[:, 12], kind="stable"):
+        dx, dy = px - P[i, 1], py - P[i, 2]
+        power = -0.5 * (P[i, 6] * dx * dx + 2.0 * P[i, 7] * dx * dy + P[i, 8] * dy * dy)
+        alpha = min(0.99, float(sc.opacities[i]) * math.exp(power))
+        assert 1.0 / 255.0 < alpha < 0.99
+        C = _quantize_numpy(C + T * alpha * P[i, 9:12], fmt)
+        T = float(_quantize_numpy(T * (1.0 - alpha), fmt))
+    opts = dict(t_cull=0.0, clamp01=True, quant=oracle.QUANT[fmt])
+    r = oracle.render(sc, cam, oracle.opts_array(per_fragment=True, **opts), pixels=[pix])
+    assert r["nfrag"][0] == 3
+    np.testing.assert_allclose(r["color"][0], C, rtol=0, atol=1e-12)
+    assert abs(r["T"][0] - T) <= 1e-12
+    store = oracle.render(sc, cam, oracle.opts_array(**opts), pixels=[pix])
+    exact = oracle.render(sc, cam, oracle.opts_array(t_cull=0.0, clamp01=True), pixels=[pix])
+    np.testing.assert_array_equal(store["color"][0], _quantize_numpy(exact["color"][0], fmt))
+    if fmt == "unorm8":   # three roundings of 1/510 each: the two emulations part
+        assert np.max(np.abs(r["color"][0] - store["color"][0])) > 0.0
+    # without a reduced format the per-fragment mode is the exact render
+    r0 = oracle.render(sc, cam, oracle.opts_array(t_cull=0.0, clamp01=True, per_fragment=True),
+                       pixels=[pix])
+    np.testing.assert_array_equal(r0["color"], exact["color"])
 
 
 def test_torch_gradcheck_on_oracle_binding():
