@@ -364,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
 
 # Gradient reduction modes of the backward raster (the paper's Sec. 3.2 ablation):
 # per-fragment atomics, and the warp reduction with balancing thresholds X.
-ABLATION = (("naive", 0), ("warp", 1), ("warp", 4), ("warp", 8), ("warp", 16), ("warp", 33))
+ABLATION = (("fragment", 0), ("naive", 0), ("warp", 1), ("warp", 4), ("warp", 8), ("warp", 16), ("warp", 33))
 
 
 def run_ablation(gs, torch, ws, ccam, state, last, dl, stream, F, reps=10):

@@ -41,7 +41,8 @@ namespace gsr {
 
 constexpr int kThreads = 128;                 // 4 independent warps per CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kStages = 4;                    // groups of 32 records in flight per warp
+constexpr int kFwdStages = 4;                 // groups of 32 records in flight per warp: forward
+constexpr int kBwdStages = 2;                 // backward (a group takes it far longer)
 constexpr unsigned kFull = 0xffffffffu;
 
 // Item encoding: block << 5 | code; code 0..3 = 16x4 band (two pixels per
@@ -49,17 +50,22 @@ constexpr unsigned kFull = 0xffffffffu;
 // on each of lanes 0..15).
 constexpr uint32_t kCell8Code = 8u, kCell4Code = 16u;
 
+template <int STAGES>
 struct WarpRing {
-  float4 a[kStages][32];
-  float4 b[kStages][32];
-  float4 c[kStages][32];
-  uint32_t rank[kStages][32];
+  static constexpr int kStages = STAGES;
+  float4 a[STAGES][32];
+  float4 b[STAGES][32];
+  float4 c[STAGES][32];
+  uint32_t rank[STAGES][32];
 };
+using FwdRing = WarpRing<kFwdStages>;
+using BwdRing = WarpRing<kBwdStages>;
 
 // Copy the records of list entries [i - lane, i - lane + 32) (this lane's is i)
 // into ring slot `slot`; `rk` is this lane's depth rank, loaded beforehand.
 // Every call commits one copy group, empty or not, so wait_group counts slots.
-__device__ __forceinline__ void ring_issue(WarpRing& R, int slot, const SplatRec* __restrict__ rec,
+template <class Ring>
+__device__ __forceinline__ void ring_issue(Ring& R, int slot, const SplatRec* __restrict__ rec,
                                            uint32_t i, uint32_t end, uint32_t rk, int lane) {
   if (i < end) {
     const SplatRec* g = rec + rk;
@@ -72,17 +78,19 @@ __device__ __forceinline__ void ring_issue(WarpRing& R, int slot, const SplatRec
 }
 
 // Fill all slots with the first kStages groups of [beg, end).
-__device__ __forceinline__ void ring_start(WarpRing& R, const SplatRec* __restrict__ rec,
+template <class Ring>
+__device__ __forceinline__ void ring_start(Ring& R, const SplatRec* __restrict__ rec,
                                            const uint32_t* __restrict__ pair_ranks, uint32_t beg,
                                            uint32_t end, int lane) {
-  uint32_t rk[kStages];
+  constexpr int S = Ring::kStages;
+  uint32_t rk[S];
 #pragma unroll
-  for (int s = 0; s < kStages; ++s) {
+  for (int s = 0; s < S; ++s) {
     const uint32_t i = beg + 32u * s + lane;
     rk[s] = i < end ? __ldg(pair_ranks + i) : 0u;
   }
 #pragma unroll
-  for (int s = 0; s < kStages; ++s) ring_issue(R, s, rec, beg + 32u * s + lane, end, rk[s], lane);
+  for (int s = 0; s < S; ++s) ring_issue(R, s, rec, beg + 32u * s + lane, end, rk[s], lane);
 }
 
 // Next item index for this warp (one atomic per warp), or >= n_items when none are left.
@@ -198,7 +206,7 @@ __device__ __forceinline__ void resume_fwd(PixelFwd& p, int x, int y, int W, int
 }
 
 template <int COLS>
-__device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict__ rec,
+__device__ __forceinline__ void fwd_item(FwdRing& R, const SplatRec* __restrict__ rec,
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
                                          int x0, int y0, int lane, int W, int H, float t_cull,
                                          int fmt, float* image, void* state, uint32_t* last_out,
@@ -221,10 +229,10 @@ __device__ __forceinline__ void fwd_item(WarpRing& R, const SplatRec* __restrict
   const uint32_t beg = range.x, end = range.y;
   if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
   int slot = 0;
-  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kStages - 1)) {
-    const uint32_t ip = gs + 32u * kStages + lane;      // this lane's entry of the refill
+  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kFwdStages - 1)) {
+    const uint32_t ip = gs + 32u * kFwdStages + lane;      // this lane's entry of the refill
     const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
-    cp_async_wait_group<kStages - 1>();
+    cp_async_wait_group<kFwdStages - 1>();
     __syncwarp();
     if (__all_sync(kFull, pa.done && pb.done)) break;
     const uint32_t cnt = min(32u, end - gs);
@@ -267,9 +275,9 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, float* __restrict__ image, void* __restrict__ state,
     uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib, int resume) {
-  __shared__ WarpRing rings[kWarps];
+  __shared__ FwdRing rings[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpRing& R = rings[warp];
+  FwdRing& R = rings[warp];
   const uint32_t n_items = hdr->n_items;
   for (uint32_t idx = next_item(next, lane); idx < n_items; idx = next_item(next, lane)) {
     int block, x0, y0;
@@ -291,129 +299,229 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
 
 // ---------------------------------------------------------------------------
 // Backward
+//
+// Procedure 1 carries C' (three channels) to form dL/dalpha_i = g . (c_i T_i -
+// C'_i) / (1 - alpha_i) (Eq. 7).  Only the dot product with g enters, so each
+// pixel carries D = g . C' instead: D_1 = g . C (stored colour), and Eq. 6
+// dotted with g gives D_{i+1} = D_i - T_i alpha_i (g . c_i).  Then
+// dL/dalpha_i = (T_i (g . c_i) - D_i) / (1 - alpha_i): the same quantity with
+// one running number per pixel instead of three.
 // ---------------------------------------------------------------------------
 
-// Sum of nine values over the warp, scattered so that each even lane ends with
-// one total: 12 shuffles instead of 45 for nine butterflies.  Lane l holds the
-// value with index  (b1 + 2 b2) + 3 b3 + 5 b4  (bits of l), valid when
-// b1 + 2 b2 < 3, (b1 + 2 b2) + 3 b3 < 5 and the index < 9.
-__device__ __forceinline__ float warp_transpose_reduce9(const float v[9], int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  float k1[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const float lo = v[i];
-    const float hi = (i + 5 < 9) ? v[i + 5] : 0.f;
-    k1[i] = (b4 ? hi : lo) + __shfl_xor_sync(kFull, b4 ? lo : hi, 16);
-  }
-  float k2[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float lo = k1[i];
-    const float hi = (i + 3 < 5) ? k1[i + 3] : 0.f;
-    k2[i] = (b3 ? hi : lo) + __shfl_xor_sync(kFull, b3 ? lo : hi, 8);
-  }
-  float k3[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float lo = k2[i];
-    const float hi = (i + 2 < 3) ? k2[i + 2] : 0.f;
-    k3[i] = (b2 ? hi : lo) + __shfl_xor_sync(kFull, b2 ? lo : hi, 4);
-  }
-  const float k4 = (b1 ? k3[1] : k3[0]) + __shfl_xor_sync(kFull, b1 ? k3[0] : k3[1], 2);
-  return k4 + __shfl_xor_sync(kFull, k4, 1);
-}
+// Reduced candidates are summed over the warp in batches of kBatch through
+// shared memory: each lane stores its nine values of a candidate in column
+// rows; after kBatch candidates, 18 lanes each add up 16 rows of one column
+// (values 0-3 or 4-7 of a candidate, or value 8 of all four) and one shuffle
+// joins the two halves.  Per candidate that is about a third of the
+// instructions of a shuffle transpose-reduce.
+constexpr int kBatch = 4;
+constexpr int kColStride = 41;   // float4 per column: 32 rows, 4 of padding between the halves,
+                                 // 41 = 1 mod 8 so that columns start in different bank groups
 
-__device__ __forceinline__ int transpose_slot(int lane) {
-  const int b1 = (lane >> 1) & 1, b2 = (lane >> 2) & 1, b3 = (lane >> 3) & 1, b4 = (lane >> 4) & 1;
-  const int i2 = b1 + 2 * b2;
-  const int i1 = i2 + 3 * b3;
-  const int v = i1 + 5 * b4;
-  return ((lane & 1) == 0 && i2 < 3 && i1 < 5 && v < 9) ? v : -1;
-}
-
-struct PixelBwd {
-  float Cp0, Cp1, Cp2, T, g0, g1, g2;
-  uint32_t end;   // depth rank after the pixel's last fragment
+struct GradBatch {
+  float4 col[9 * kColStride];
+  uint32_t rank[kBatch];
 };
 
-// chunk_state (memory-efficiency mode): with chunk_in, (C', T) continue from the
-// previous chunk instead of (stored C, 1).
-__device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, int y, int W,
-                                               int fmt, const void* state,
-                                               const uint32_t* last_in, const float* dLdC,
-                                               const float4* chunk_state, int chunk_in) {
-  p.Cp0 = p.Cp1 = p.Cp2 = 0.f;
-  p.g0 = p.g1 = p.g2 = 0.f;
-  p.T = 1.f;
-  p.end = 0;
-  if (valid) {
-    const size_t pix = (size_t)y * W + x;
-    if (chunk_in) {
-      const float4 cs = chunk_state[pix];
-      p.Cp0 = cs.x; p.Cp1 = cs.y; p.Cp2 = cs.z; p.T = cs.w;
-    } else {
-      const float4 st = load_state(state, fmt, pix);
-      p.Cp0 = st.x; p.Cp1 = st.y; p.Cp2 = st.z;
-    }
-    p.g0 = dLdC[3 * pix]; p.g1 = dLdC[3 * pix + 1]; p.g2 = dLdC[3 * pix + 2];
-    const uint32_t l = last_in[pix];
-    p.end = (l == kNone) ? 0u : l + 1u;
-  }
+// Row position of lane `lane` in a column: rows 16..31 sit four float4 later,
+// so that the two halves read in one step fall in different bank groups.
+__device__ __forceinline__ int batch_row(int lane) { return lane + ((lane >> 4) << 2); }
+
+__device__ __forceinline__ void batch_put(GradBatch& B, int s, int lane, uint32_t rank,
+                                          const float v[9]) {
+  const int row = batch_row(lane);
+  B.col[(2 * s) * kColStride + row] = make_float4(v[0], v[1], v[2], v[3]);
+  B.col[(2 * s + 1) * kColStride + row] = make_float4(v[4], v[5], v[6], v[7]);
+  reinterpret_cast<float*>(&B.col[8 * kColStride + row])[s] = v[8];
+  if (lane == 0) B.rank[s] = rank;
 }
 
-// One fragment of Procedure 1 plus the chain rule to the 2D parameters; the
-// nine values are added into v.  The pixel's fragments are exactly the hits
-// below its end rank: the forward stopped after the fragment that took T
-// under t_cull, and the same arithmetic in the same order gives the same T
-// here, so Procedure 1's cull test needs no second evaluation.
-//
-// A missed pixel (hit false) runs the same code with G = 0: every term is an
-// exact zero and the state is unchanged, so a warp handles both of a lane's
-// pixels without branching.  FIRST writes v instead of adding to it.
-template <bool FIRST>
-__device__ __forceinline__ void grad_fragment(PixelBwd& p, bool hit, float q, float y1, float y2,
-                                              const float4& a, const float4& b, const float4& c,
-                                              float v[9]) {
-  float G, at;
-  const float alpha = frag_alpha_masked(hit, c.w, q, G, at);
-  const float oma = __fsub_rn(1.0f, alpha);
-  const float wT = __fmul_rn(alpha, p.T);
-  float t[9];
-  // Eq. 3
-  t[5] = p.g0 * wT;
-  t[6] = p.g1 * wT;
-  t[7] = p.g2 * wT;
-  // Eq. 7 with C'_i before its update
-  const float dLda = (p.g0 * (c.x * p.T - p.Cp0) + p.g1 * (c.y * p.T - p.Cp1) +
-                      p.g2 * (c.z * p.T - p.Cp2)) * __fdividef(1.0f, oma);
-  // Eq. 6, Eq. 5
-  p.Cp0 -= wT * c.x;
-  p.Cp1 -= wT * c.y;
-  p.Cp2 -= wT * c.z;
-  p.T = next_T(p.T, alpha);
-  // alpha = min(0.99, o G): no gradient through the clamp
-  const float d_at = at < kAlphaMax ? dLda : 0.f;
-  t[8] = G * d_at;
-  // z = Sigma^-1 d = L^-T L^-1 d, in units of 1 / (2 ln 2):
-  // dpower/dmu_2D = z and dpower/dSigma_2D = z z^T / 2
-  const float w = at * d_at;
-  const float z1 = b.x * y2;
-  const float z0 = a.z * y1 - a.w * z1;
-  const float wz0 = w * z0, wz1 = w * z1;
-  t[0] = wz0;
-  t[1] = wz1;
-  t[2] = wz0 * z0;
-  t[3] = wz0 * z1;
-  t[4] = wz1 * z1;
+// Sums of the batch's first n candidates, added to their accumulators.
+__device__ __forceinline__ void batch_flush(GradBatch& B, int n, int lane, float* g2d) {
+  __syncwarp();
+  const int c = min(lane & 15, 8), half = lane >> 4;
+  const float4* src = &B.col[c * kColStride + half * 20];
+  float4 acc = src[0];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) v[k] = FIRST ? t[k] : v[k] + t[k];
+  for (int r = 1; r < 16; ++r) {
+    const float4 v = src[r];
+    acc.x += v.x;
+    acc.y += v.y;
+    acc.z += v.z;
+    acc.w += v.w;
+  }
+  acc.x += __shfl_xor_sync(kFull, acc.x, 16);
+  acc.y += __shfl_xor_sync(kFull, acc.y, 16);
+  acc.z += __shfl_xor_sync(kFull, acc.z, 16);
+  acc.w += __shfl_xor_sync(kFull, acc.w, 16);
+  if (lane < 8) {
+    const int s = lane >> 1;
+    if (s < n) red_add_v4(g2d + (size_t)B.rank[s] * 12 + 4 * (lane & 1), acc.x, acc.y, acc.z, acc.w);
+  } else if (lane == 8) {   // value 8 of each candidate
+    atomicAdd(g2d + (size_t)B.rank[0] * 12 + 8, acc.x);
+    if (n > 1) atomicAdd(g2d + (size_t)B.rank[1] * 12 + 8, acc.y);
+    if (n > 2) atomicAdd(g2d + (size_t)B.rank[2] * 12 + 8, acc.z);
+    if (n > 3) atomicAdd(g2d + (size_t)B.rank[3] * 12 + 8, acc.w);
+  }
+  __syncwarp();   // the columns are free again
 }
 
 __device__ __forceinline__ void red_add9(float* dst, const float v[9]) {
   red_add_v4(dst, v[0], v[1], v[2], v[3]);
   red_add_v4(dst + 4, v[4], v[5], v[6], v[7]);
   red_add_v4(dst + 8, v[8], 0.f, 0.f, 0.f);
+}
+
+// Candidate `rank`'s nine values v of this lane (frag: the lane had a
+// fragment): added directly when fewer than `threshold` lanes have one (the
+// balancing threshold of Sec. 3.2.4), else put in the batch (nb: candidates
+// waiting in it).
+template <int MODE>
+__device__ __forceinline__ void reduce_candidate(const float v[9], bool frag, uint32_t rank,
+                                                 GradBatch& B, int& nb, float* g2d,
+                                                 int threshold, int lane) {
+  if (MODE != GS_REDUCE_WARP) {
+    if (frag) red_add9(g2d + (size_t)rank * 12, v);
+  } else {
+    const uint32_t active = __ballot_sync(kFull, frag);
+    if (active != 0u) {
+      if (__popc(active) < threshold) {
+        if (frag) red_add9(g2d + (size_t)rank * 12, v);
+      } else {
+        batch_put(B, nb, lane, rank, v);
+        if (++nb == kBatch) {
+          batch_flush(B, kBatch, lane, g2d);
+          nb = 0;
+        }
+      }
+    }
+  }
+}
+
+struct PixelBwd {
+  float D, T, g0, g1, g2;   // D = g . C'
+  uint32_t end;             // depth rank after the pixel's last fragment
+};
+
+// chunk_state (memory-efficiency mode): with chunk_in, (D, T) continue from the
+// previous chunk instead of (g . stored C, 1).
+__device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, int y, int W,
+                                               int fmt, const void* state,
+                                               const uint32_t* last_in, const float* dLdC,
+                                               const float4* chunk_state, int chunk_in) {
+  p.D = 0.f;
+  p.g0 = p.g1 = p.g2 = 0.f;
+  p.T = 1.f;
+  p.end = 0;
+  if (valid) {
+    const size_t pix = (size_t)y * W + x;
+    p.g0 = dLdC[3 * pix]; p.g1 = dLdC[3 * pix + 1]; p.g2 = dLdC[3 * pix + 2];
+    if (chunk_in) {
+      const float4 cs = chunk_state[pix];
+      p.D = cs.x;
+      p.T = cs.y;
+    } else {
+      const float4 st = load_state(state, fmt, pix);
+      p.D = p.g0 * st.x + p.g1 * st.y + p.g2 * st.z;
+    }
+    const uint32_t l = last_in[pix];
+    p.end = (l == kNone) ? 0u : l + 1u;
+  }
+}
+
+// One fragment of Procedure 1 plus the chain rule to the 2D parameters; the
+// nine values go to v.  The pixel's fragments are exactly the hits below its
+// end rank: the forward stopped after the fragment that took T under t_cull,
+// so Procedure 1's cull test needs no second evaluation.  A missed pixel (hit
+// false) runs the same code with G = 0: every term is an exact zero and the
+// state is unchanged.
+__device__ __forceinline__ void grad_fragment(PixelBwd& p, bool hit, float q, float y1, float y2,
+                                              const float4& a, const float4& b, const float4& c,
+                                              float v[9]) {
+  float G, at;
+  const float alpha = frag_alpha_masked(hit, c.w, q, G, at);
+  const float oma = __fsub_rn(1.0f, alpha);
+  const float wT = alpha * p.T;
+  // Eq. 3
+  v[5] = p.g0 * wT;
+  v[6] = p.g1 * wT;
+  v[7] = p.g2 * wT;
+  // Eq. 7 with D_i = g . C'_i before its update, then Eq. 6 and Eq. 5
+  const float gc = p.g0 * c.x + p.g1 * c.y + p.g2 * c.z;
+  const float dLda = (p.T * gc - p.D) * __fdividef(1.0f, oma);
+  p.D -= wT * gc;
+  p.T = next_T(p.T, alpha);
+  // alpha = min(0.99, o G): no gradient through the clamp
+  const float d_at = at < kAlphaMax ? dLda : 0.f;
+  v[8] = G * d_at;
+  // z = Sigma^-1 d = L^-T L^-1 d, in units of 1 / (2 ln 2):
+  // dpower/dmu_2D = z and dpower/dSigma_2D = z z^T / 2
+  const float w = at * d_at;
+  const float z1 = b.x * y2;
+  const float z0 = a.z * y1 - a.w * z1;
+  const float wz0 = w * z0, wz1 = w * z1;
+  v[0] = wz0;
+  v[1] = wz1;
+  v[2] = wz0 * z0;
+  v[3] = wz0 * z1;
+  v[4] = wz1 * z1;
+}
+
+// One warp, one footprint COLS x 4 with one pixel per lane (COLS = 8 or 4).
+template <int COLS, int MODE>
+__device__ __forceinline__ void bwd_item(BwdRing& R, GradBatch& B,
+                                         const SplatRec* __restrict__ rec,
+                                         const uint32_t* __restrict__ pair_ranks, uint2 range,
+                                         int x0, int y0, int lane, int W, int H, int fmt,
+                                         const void* state, const uint32_t* last_in,
+                                         const float* dLdC, float* g2d, int threshold,
+                                         float4* chunk_state, int chunk_in, int chunk_out) {
+  int x, ya;
+  bool own;
+  lane_pixels<COLS>(x0, y0, lane, x, ya, own);
+  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f;
+  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
+  PixelBwd pa;
+  const bool va = own && x < W && ya < H;
+  load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
+  // depth ranks >= this contribute nowhere in the footprint
+  const uint32_t warp_end = __reduce_max_sync(kFull, pa.end);
+
+  const uint32_t beg = range.x, end = warp_end > 0u ? range.y : range.x;
+  if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
+  int slot = 0, nb = 0;
+  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kBwdStages - 1)) {
+    const uint32_t ip = gs + 32u * kBwdStages + lane;
+    const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
+    cp_async_wait_group<kBwdStages - 1>();
+    __syncwarp();
+    if (R.rank[slot][0] >= warp_end) break;   // ranks ascend along the list
+    const uint32_t cnt = min(32u, end - gs);
+    uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
+                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
+                                                       (float)(COLS - 1), 3.f));
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const uint32_t rank = R.rank[slot][j];
+      const float4 a = R.a[slot][j];
+      const float4 b = R.b[slot][j];
+      float y1, y2;
+      const float q = frag_q(px, pya, a, b, y1, y2);
+      const bool ha = rank < pa.end && q <= b.y;
+      if (!__any_sync(kFull, ha)) continue;
+      const float4 c = R.c[slot][j];
+      float v[9];
+      grad_fragment(pa, ha, q, y1, y2, a, b, c, v);
+      reduce_candidate<MODE>(v, ha, rank, B, nb, g2d, threshold, lane);
+    }
+    __syncwarp();   // every lane is done with the slot before it is refilled
+    ring_issue(R, slot, rec, ip, end, rk_next, lane);
+  }
+  cp_async_wait_all();
+  if (nb > 0) batch_flush(B, nb, lane, g2d);
+  __syncwarp();
+  if (chunk_out && va) chunk_state[(size_t)ya * W + x] = make_float4(pa.D, pa.T, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -435,16 +543,14 @@ __device__ __forceinline__ float2 frag_q_pair(float px, float2 py, const float4&
 }
 
 struct PairBwd {
-  float2 nC0, nC1, nC2;   // -C' of the two pixels (Eq. 6 then adds T alpha c)
+  float2 nD;              // -D = -g . C' of the two pixels
   float2 T, g0, g1, g2;
   uint32_t end_a, end_b;  // depth rank after each pixel's last fragment
 };
 
 __device__ __forceinline__ PairBwd pack_pair(const PixelBwd& a, const PixelBwd& b) {
   PairBwd p;
-  p.nC0 = make_float2(-a.Cp0, -b.Cp0);
-  p.nC1 = make_float2(-a.Cp1, -b.Cp1);
-  p.nC2 = make_float2(-a.Cp2, -b.Cp2);
+  p.nD = make_float2(-a.D, -b.D);
   p.T = make_float2(a.T, b.T);
   p.g0 = make_float2(a.g0, b.g0);
   p.g1 = make_float2(a.g1, b.g1);
@@ -454,9 +560,8 @@ __device__ __forceinline__ PairBwd pack_pair(const PixelBwd& a, const PixelBwd& 
   return p;
 }
 
-// One candidate of Procedure 1 at both pixels of a lane, as grad_fragment:
-// a missed pixel runs with G = 0, which leaves its state unchanged and gives
-// exact zeros.  t[k] holds the two pixels' contributions to value k.
+// One candidate of Procedure 1 at both pixels of a lane, as grad_fragment.
+// t[k] holds the two pixels' contributions to value k.
 __device__ __forceinline__ void grad_pair(PairBwd& p, bool ha, bool hb, float2 q, float y1,
                                           float2 y2, const float4& a, const float4& b,
                                           const float4& c, float2 t[9]) {
@@ -469,17 +574,12 @@ __device__ __forceinline__ void grad_pair(PairBwd& p, bool ha, bool hb, float2 q
   t[5] = __fmul2_rn(p.g0, wT);
   t[6] = __fmul2_rn(p.g1, wT);
   t[7] = __fmul2_rn(p.g2, wT);
-  // Eq. 7 with C'_i before its update: g . (c T - C') / (1 - alpha)
-  const float2 e0 = __ffma2_rn(f2(c.x), p.T, p.nC0);
-  const float2 e1 = __ffma2_rn(f2(c.y), p.T, p.nC1);
-  const float2 e2 = __ffma2_rn(f2(c.z), p.T, p.nC2);
-  const float2 gs = __ffma2_rn(p.g0, e0, __ffma2_rn(p.g1, e1, __fmul2_rn(p.g2, e2)));
-  const float2 dLda =
-      __fmul2_rn(gs, make_float2(__fdividef(1.0f, oma.x), __fdividef(1.0f, oma.y)));
-  // Eq. 6, Eq. 5
-  p.nC0 = __ffma2_rn(wT, f2(c.x), p.nC0);
-  p.nC1 = __ffma2_rn(wT, f2(c.y), p.nC1);
-  p.nC2 = __ffma2_rn(wT, f2(c.z), p.nC2);
+  // Eq. 7 with D_i before its update: (T g . c - D) / (1 - alpha)
+  const float2 gc = __ffma2_rn(p.g0, f2(c.x), __ffma2_rn(p.g1, f2(c.y), __fmul2_rn(p.g2, f2(c.z))));
+  const float2 dLda = __fmul2_rn(__ffma2_rn(p.T, gc, p.nD),
+                                 make_float2(__fdividef(1.0f, oma.x), __fdividef(1.0f, oma.y)));
+  // Eq. 6 (dotted with g), Eq. 5
+  p.nD = __ffma2_rn(wT, gc, p.nD);
   p.T = __fmul2_rn(p.T, oma);
   // alpha = min(0.99, o G): no gradient through the clamp
   const float2 d_at = make_float2(at.x < kAlphaMax ? dLda.x : 0.0f, at.y < kAlphaMax ? dLda.y : 0.0f);
@@ -495,128 +595,11 @@ __device__ __forceinline__ void grad_pair(PairBwd& p, bool ha, bool hb, float2 q
   t[4] = __fmul2_rn(t[1], z1);
 }
 
-// Candidate j's nine values v of this lane (frag: the lane had a fragment):
-// added directly when fewer than `threshold` lanes have one (Sec. 3.2.4),
-// else summed over the warp into part[j] and marked in `reduced`.
+// The 16x4 band (two pixels per lane) with the pixel pair packed; in
+// GS_REDUCE_FRAGMENT mode each pixel's fragment adds its own values to the
+// splat's accumulators.
 template <int MODE>
-__device__ __forceinline__ void reduce_candidate(const float v[9], bool frag, int j, uint32_t rank,
-                                                 float (*part)[12], float* g2d, int threshold,
-                                                 int tslot, int lane, uint32_t& reduced) {
-  if (MODE != GS_REDUCE_WARP) {
-    if (frag) red_add9(g2d + (size_t)rank * 12, v);
-  } else {
-    const uint32_t active = __ballot_sync(kFull, frag);
-    if (active != 0u) {
-      if (__popc(active) < threshold) {
-        if (frag) red_add9(g2d + (size_t)rank * 12, v);
-      } else {
-        const float tot = warp_transpose_reduce9(v, lane);
-        if (tslot >= 0) part[j][tslot] = tot;
-        reduced |= 1u << j;
-      }
-    }
-  }
-}
-
-// One vector-atomic triple per reduced candidate of the group: lane j adds
-// candidate j's totals.
-template <int MODE>
-__device__ __forceinline__ void flush_reduced(float (*part)[12], const WarpRing& R, int slot,
-                                              uint32_t reduced, float* g2d, int lane) {
-  if (MODE != GS_REDUCE_WARP || !reduced) return;
-  __syncwarp();
-  if ((reduced >> lane) & 1u) {
-    const float4* p = reinterpret_cast<const float4*>(part[lane]);
-    float* gdst = g2d + (size_t)R.rank[slot][lane] * 12;
-    const float4 p0 = p[0], p1 = p[1], p2 = p[2];
-    red_add_v4(gdst, p0.x, p0.y, p0.z, p0.w);
-    red_add_v4(gdst + 4, p1.x, p1.y, p1.z, p1.w);
-    red_add_v4(gdst + 8, p2.x, p2.y, p2.z, p2.w);
-  }
-}
-
-// part: this warp's 32 x 12 partial sums (slots 9..11 stay zero).
-template <int COLS, int MODE>
-__device__ __forceinline__ void bwd_item(WarpRing& R, float (*part)[12],
-                                         const SplatRec* __restrict__ rec,
-                                         const uint32_t* __restrict__ pair_ranks, uint2 range,
-                                         int x0, int y0, int lane, int W, int H, int fmt,
-                                         const void* state, const uint32_t* last_in,
-                                         const float* dLdC, float* g2d, int threshold,
-                                         float4* chunk_state, int chunk_in, int chunk_out) {
-  constexpr int NPX = COLS == 16 ? 2 : 1;
-  int x, ya;
-  bool own;
-  lane_pixels<COLS>(x0, y0, lane, x, ya, own);
-  const int yb = ya + 2;
-  const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
-  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
-  const int tslot = transpose_slot(lane);
-  PixelBwd pa, pb;
-  const bool va = own && x < W && ya < H, vb = NPX == 2 && x < W && yb < H;
-  load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
-  if (NPX == 2) {
-    load_pixel_bwd(pb, vb, x, yb, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
-  } else {
-    pb.Cp0 = pb.Cp1 = pb.Cp2 = 0.f;
-    pb.g0 = pb.g1 = pb.g2 = 0.f;
-    pb.T = 1.f;
-    pb.end = 0u;
-  }
-  // depth ranks >= this contribute nowhere in the footprint
-  const uint32_t warp_end = __reduce_max_sync(kFull, max(pa.end, pb.end));
-
-  const uint32_t beg = range.x, end = warp_end > 0u ? range.y : range.x;
-  if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
-  int slot = 0;
-  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kStages - 1)) {
-    const uint32_t ip = gs + 32u * kStages + lane;
-    const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
-    cp_async_wait_group<kStages - 1>();
-    __syncwarp();
-    if (R.rank[slot][0] >= warp_end) break;   // ranks ascend along the list
-    const uint32_t cnt = min(32u, end - gs);
-    uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
-                                          rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
-                                                       (float)(COLS - 1), 3.f));
-    uint32_t reduced = 0u;   // candidates whose warp sums wait in `part`
-    while (m) {
-      const int j = __ffs(m) - 1;
-      m &= m - 1u;
-      const uint32_t rank = R.rank[slot][j];
-      const float4 a = R.a[slot][j];
-      const float4 b = R.b[slot][j];
-      float y1, y2a, y2b = 0.f, qa, qb = 0.f;
-      if (NPX == 2)
-        frag_q2(px, pya, pyb, a, b, y1, y2a, y2b, qa, qb);
-      else
-        qa = frag_q(px, pya, a, b, y1, y2a);
-      const bool ha = rank < pa.end && qa <= b.y;
-      const bool hb = NPX == 2 && rank < pb.end && qb <= b.y;
-      if (!__any_sync(kFull, ha || hb)) continue;
-      const float4 c = R.c[slot][j];
-      float v[9];
-      grad_fragment<true>(pa, ha, qa, y1, y2a, a, b, c, v);
-      if (NPX == 2) grad_fragment<false>(pb, hb, qb, y1, y2b, a, b, c, v);
-      reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
-    }
-    flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
-    __syncwarp();   // every lane is done with the slot and `part` before they are reused
-    ring_issue(R, slot, rec, ip, end, rk_next, lane);
-  }
-  cp_async_wait_all();
-  __syncwarp();
-  if (chunk_out) {
-    if (va) chunk_state[(size_t)ya * W + x] = make_float4(pa.Cp0, pa.Cp1, pa.Cp2, pa.T);
-    if (vb) chunk_state[(size_t)yb * W + x] = make_float4(pb.Cp0, pb.Cp1, pb.Cp2, pb.T);
-  }
-}
-
-// The 16x4 band (two pixels per lane) of bwd_item with the pixel pair packed
-// (grad_pair); in GS_REDUCE_FRAGMENT mode each pixel's fragment adds its own
-// values to the splat's accumulators.
-template <int MODE>
-__device__ __forceinline__ void bwd_item_pair(WarpRing& R, float (*part)[12],
+__device__ __forceinline__ void bwd_item_pair(BwdRing& R, GradBatch& B,
                                               const SplatRec* __restrict__ rec,
                                               const uint32_t* __restrict__ pair_ranks,
                                               uint2 range, int x0, int y0, int lane, int W,
@@ -631,7 +614,6 @@ __device__ __forceinline__ void bwd_item_pair(WarpRing& R, float (*part)[12],
   const float px = (float)x + 0.5f;
   const float2 py = make_float2((float)ya + 0.5f, (float)yb + 0.5f);
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
-  const int tslot = transpose_slot(lane);
   const bool va = x < W && ya < H, vb = x < W && yb < H;
   PairBwd pp;
   {
@@ -645,18 +627,17 @@ __device__ __forceinline__ void bwd_item_pair(WarpRing& R, float (*part)[12],
 
   const uint32_t beg = range.x, end = warp_end > 0u ? range.y : range.x;
   if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
-  int slot = 0;
-  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kStages - 1)) {
-    const uint32_t ip = gs + 32u * kStages + lane;
+  int slot = 0, nb = 0;
+  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kBwdStages - 1)) {
+    const uint32_t ip = gs + 32u * kBwdStages + lane;
     const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
-    cp_async_wait_group<kStages - 1>();
+    cp_async_wait_group<kBwdStages - 1>();
     __syncwarp();
     if (R.rank[slot][0] >= warp_end) break;   // ranks ascend along the list
     const uint32_t cnt = min(32u, end - gs);
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
                                                        15.f, 3.f));
-    uint32_t reduced = 0u;   // candidates whose warp sums wait in `part`
     while (m) {
       const int j = __ffs(m) - 1;
       m &= m - 1u;
@@ -685,18 +666,18 @@ __device__ __forceinline__ void bwd_item_pair(WarpRing& R, float (*part)[12],
         float v[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) v[k] = t[k].x + t[k].y;
-        reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
+        reduce_candidate<MODE>(v, ha || hb, rank, B, nb, g2d, threshold, lane);
       }
     }
-    flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
-    __syncwarp();   // every lane is done with the slot and `part` before they are reused
+    __syncwarp();   // every lane is done with the slot before it is refilled
     ring_issue(R, slot, rec, ip, end, rk_next, lane);
   }
   cp_async_wait_all();
+  if (nb > 0) batch_flush(B, nb, lane, g2d);
   __syncwarp();
   if (chunk_out) {
-    if (va) chunk_state[(size_t)ya * W + x] = make_float4(-pp.nC0.x, -pp.nC1.x, -pp.nC2.x, pp.T.x);
-    if (vb) chunk_state[(size_t)yb * W + x] = make_float4(-pp.nC0.y, -pp.nC1.y, -pp.nC2.y, pp.T.y);
+    if (va) chunk_state[(size_t)ya * W + x] = make_float4(-pp.nD.x, pp.T.x, 0.f, 0.f);
+    if (vb) chunk_state[(size_t)yb * W + x] = make_float4(-pp.nD.y, pp.T.y, 0.f, 0.f);
   }
 }
 
@@ -796,7 +777,7 @@ __device__ __forceinline__ void back_group(uint32_t k, uint32_t beg, uint32_t st
 }
 
 template <int COLS, int MODE>
-__device__ __forceinline__ void bwd_item_back(WarpRing& R, float (*part)[12],
+__device__ __forceinline__ void bwd_item_back(BwdRing& R, GradBatch& B,
                                               const SplatRec* __restrict__ rec,
                                               const uint32_t* __restrict__ pair_ranks,
                                               uint2 range, int x0, int y0, int lane, int W, int H,
@@ -810,7 +791,6 @@ __device__ __forceinline__ void bwd_item_back(WarpRing& R, float (*part)[12],
   const int yb = ya + 2;
   const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
-  const int tslot = transpose_slot(lane);
   PixelBack pa, pb;
   load_pixel_back(pa, own && x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
   if (NPX == 2) {
@@ -825,31 +805,30 @@ __device__ __forceinline__ void bwd_item_back(WarpRing& R, float (*part)[12],
   if (warp_end == 0u) return;
   const uint32_t beg = range.x;
   const uint32_t stop = first_rank_at_least(pair_ranks, range.x, range.y, warp_end, lane);
-  // prologue: the last kStages groups before `stop`
+  // prologue: the last kBwdStages groups before `stop`
 #pragma unroll
-  for (int s = 0; s < kStages; ++s) {
+  for (int s = 0; s < kBwdStages; ++s) {
     uint32_t glo, ghi;
     back_group((uint32_t)s, beg, stop, glo, ghi);
     const uint32_t i = glo + (uint32_t)lane;
     const uint32_t rk = i < ghi ? __ldg(pair_ranks + i) : 0u;
     ring_issue(R, s, rec, i, ghi, rk, lane);
   }
-  int slot = 0;
-  for (uint32_t k = 0;; ++k, slot = (slot + 1) & (kStages - 1)) {
+  int slot = 0, nb = 0;
+  for (uint32_t k = 0;; ++k, slot = (slot + 1) & (kBwdStages - 1)) {
     uint32_t glo, ghi;
     back_group(k, beg, stop, glo, ghi);
     if (glo >= ghi) break;
     uint32_t nlo, nhi;
-    back_group(k + kStages, beg, stop, nlo, nhi);
+    back_group(k + kBwdStages, beg, stop, nlo, nhi);
     const uint32_t ip = nlo + (uint32_t)lane;
     const uint32_t rk_next = ip < nhi ? __ldg(pair_ranks + ip) : 0u;
-    cp_async_wait_group<kStages - 1>();
+    cp_async_wait_group<kBwdStages - 1>();
     __syncwarp();
     const uint32_t cnt = ghi - glo;
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
                                                        (float)(COLS - 1), 3.f));
-    uint32_t reduced = 0u;
     while (m) {
       const int j = 31 - __clz(m);   // deepest first
       m &= ~(1u << j);
@@ -869,13 +848,13 @@ __device__ __forceinline__ void bwd_item_back(WarpRing& R, float (*part)[12],
         if (ha) grad_fragment_back(pa, qa, y1a, y2a, a, b, c, v);
         if (NPX == 2 && hb) grad_fragment_back(pb, qb, y1b, y2b, a, b, c, v);
       }
-      reduce_candidate<MODE>(v, ha || hb, j, rank, part, g2d, threshold, tslot, lane, reduced);
+      reduce_candidate<MODE>(v, ha || hb, rank, B, nb, g2d, threshold, lane);
     }
-    flush_reduced<MODE>(part, R, slot, reduced, g2d, lane);
     __syncwarp();
     ring_issue(R, slot, rec, ip, nhi, rk_next, lane);
   }
   cp_async_wait_all();
+  if (nb > 0) batch_flush(B, nb, lane, g2d);
   __syncwarp();
 }
 
@@ -887,16 +866,11 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     float t_cull, int fmt, const void* __restrict__ state, const uint32_t* __restrict__ last_in,
     const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold, int back,
     float4* __restrict__ chunk_state, int chunk_in, int chunk_out) {
-  __shared__ WarpRing rings[kWarps];
-  __shared__ __align__(16) float s_part[kWarps][32][12];
+  __shared__ BwdRing rings[kWarps];
+  __shared__ GradBatch batches[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpRing& R = rings[warp];
-  float (*part)[12] = s_part[warp];
-  // padding slots 9..11 of the partial sums stay zero
-  part[lane][9] = 0.f;
-  part[lane][10] = 0.f;
-  part[lane][11] = 0.f;
-  __syncwarp();
+  BwdRing& R = rings[warp];
+  GradBatch& B = batches[warp];
   const uint32_t n_items = hdr->n_items;
   for (uint32_t idx = next_item(next, lane); idx < n_items; idx = next_item(next, lane)) {
     int block, x0, y0;
@@ -904,24 +878,24 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     const uint2 range = ranges[block];
     if (back) {
       if (cols == 16)
-        bwd_item_back<16, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+        bwd_item_back<16, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                                 last_in, dLdC, g2d, threshold);
       else if (cols == 8)
-        bwd_item_back<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+        bwd_item_back<8, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                                last_in, dLdC, g2d, threshold);
       else
-        bwd_item_back<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+        bwd_item_back<4, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                                last_in, dLdC, g2d, threshold);
       continue;
     }
     if (cols == 16)
-      bwd_item_pair<MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+      bwd_item_pair<MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                           last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
     else if (cols == 8)
-      bwd_item<8, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+      bwd_item<8, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                         last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
     else
-      bwd_item<4, MODE>(R, part, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
+      bwd_item<4, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
                         last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
   }
 }

@@ -53,20 +53,52 @@ def test_fullsize_sampled_pixels(full_view):
           f"max-abs {err[ok].max():.2e}")
 
 
+def _stratified_splats(ws, rng, per_stratum=16):
+    """Depth ranks of sampled splats in three strata: large footprints (boxes
+    over 8 blocks, at most 36), splats on the 20 longest block lists (the
+    blocks walked by 8x4 and 4x4 footprints at the default split threshold;
+    taken from the first 256 entries of each list, which are not T-culled
+    everywhere), and the rest (boxes of at most 8 blocks)."""
+    V = gs.read_counters(ws)["visible"]
+    boxes = gs.copy_array(ws, gs._lib.GS_ARRAY_BOXES, V).cpu().numpy().astype(np.int64)
+    nblk = (boxes[:, 1] & 0xFFFF) * (boxes[:, 1] >> 16)
+    big = rng.choice(np.where((nblk > 8) & (nblk <= 36))[0], size=per_stratum, replace=False)
+    nb = gs.read_counters(ws)["blocks"]
+    ranges = gs.copy_array(ws, gs._lib.GS_ARRAY_RANGES, nb).cpu().numpy().astype(np.int64)
+    ranges = ranges.reshape(-1, 2) & 0xFFFFFFFF
+    lens = ranges[:, 1] - ranges[:, 0]
+    longest = np.argsort(-lens, kind="stable")[:20]
+    live = gs.read_counters(ws)["live_pairs"]
+    pair_ranks = gs.copy_array(ws, gs._lib.GS_ARRAY_PAIR_RANKS, live).cpu().numpy().astype(np.int64)
+    on_long = np.unique(np.concatenate([pair_ranks[b:min(b + 256, e)] for b, e in ranges[longest]]))
+    on_long = np.setdiff1d(on_long, big)
+    dense = rng.choice(on_long, size=per_stratum, replace=False)
+    rest = np.setdiff1d(np.where(nblk <= 8)[0], np.concatenate([big, dense]))
+    other = rng.choice(rest, size=per_stratum, replace=False)
+    return dict(large=big, long_lists=dense, other=other), int(lens[longest[-1]])
+
+
 def test_fullsize_sampled_splat_gradients(full_view):
+    """Complete gradients of 48 sampled splats at the benchmark's size and launch
+    configuration, stratified by footprint, against the oracle one splat at a
+    time (each traced over its own pixels)."""
     v = full_view
     cam = v["cam"]
     ws = v["ws"]
     V = gs.read_counters(ws)["visible"]
     ids = gs.copy_array(ws, gs._lib.GS_ARRAY_SORTED_IDS, V).cpu().numpy()
-    boxes = gs.copy_array(ws, gs._lib.GS_ARRAY_BOXES, V).cpu().numpy().astype(np.int64)
-    nblk = (boxes[:, 1] & 0xFFFF) * (boxes[:, 1] >> 16)   # footprint in 16x16 blocks
-    rng = np.random.default_rng(302)
-    cand = np.where(nblk <= 2)[0]
-    pick = ids[rng.choice(cand, size=12, replace=False)]
+    strata, shortest_long = _stratified_splats(ws, np.random.default_rng(302))
+    assert shortest_long >= gs._lib.GS_SPLIT_THRESHOLD_DEFAULT   # those blocks take split footprints
+    pick = ids[np.concatenate(list(strata.values()))]
     ref = oracle.splat_grads(v["scene_np"], cam, v["g"].astype(np.float64), pick,
                              oracle_opts(v["opts"], cam))
-    errs = {k: rel_l2(v["grads"][k][pick], ref[k]) for k in GROUPS}
-    print("sampled splat gradient rel-L2:", errs)
-    for k, e in errs.items():
-        assert e <= 1e-3, f"{k}: {e:.3e}"
+    lo = 0
+    for name, ranks in strata.items():
+        sl = slice(lo, lo + len(ranks))
+        lo += len(ranks)
+        errs = {k: rel_l2(v["grads"][k][pick[sl]], ref[k][sl]) for k in GROUPS}
+        print(f"{name}: {len(ranks)} splats, {int(ref['pixels'][sl].sum())} traced pixels, "
+              f"gradient rel-L2 {errs}")
+        assert np.linalg.norm(ref["opacities"][sl]) > 0.0, name
+        for k, e in errs.items():
+            assert e <= 1e-3, f"{name} {k}: {e:.3e}"

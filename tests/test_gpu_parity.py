@@ -162,12 +162,18 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
 # ---------------------------------------------------------------------------
 
 def _check_forward(scene_np, cam, opts, max_ambig_frac=0.2):
+    """Image, transmittance, fragment count and last fragment against the oracle
+    on every pixel outside the tie bands.  The flagged fraction is printed, with
+    how many flagged pixels actually differ (a decision at a band taken the other
+    way) so that a widening band cannot hide errors unnoticed."""
     scene, ws, out = run_forward(scene_np, cam, opts)
     ref = oracle.render(scene_np, cam, oracle_opts(opts, cam))
     ok = (ref["ambig"] & AMBIG_IMAGE) == 0
-    assert ok.mean() >= 1.0 - max_ambig_frac, f"too many tie-band pixels: {1 - ok.mean():.3f}"
     img = out["image"].cpu().numpy().astype(np.float64)
     err = np.abs(img - ref["color"]).max(axis=2)
+    print(f"tie-band pixels {int((~ok).sum())}/{ok.size} ({1 - ok.mean():.4%}), "
+          f"of which {int((err[~ok] > 1e-4).sum())} differ by more than 1e-4")
+    assert ok.mean() >= 1.0 - max_ambig_frac, f"too many tie-band pixels: {1 - ok.mean():.4f}"
     assert err[ok].max() <= 1e-4, f"image max-abs {err[ok].max():.3e}"
     st = gs.decode_state(out["state"], "fp32").cpu().numpy() if opts.state_format == "fp32" else None
     if st is not None:
@@ -178,9 +184,15 @@ def _check_forward(scene_np, cam, opts, max_ambig_frac=0.2):
     return scene, ws, out, ref, ok
 
 
+# Tie bands on the 1,024-splat 128x128 scene: 20 of 16,384 pixels (0.12%), all
+# within 5e-4 of a splat's alpha = 1/255 cut in power (a ring ~4e-4 px wide
+# around each of 1,024 ellipses of ~4.6 px radius: ~12 pixel centres expected).
+TINY_BAND_FRAC = 0.003
+
+
 def test_forward_tiny_scene():
     scene_np, cam, _ = syn.tiny_scene_1k()
-    _check_forward(scene_np, cam, gs.RasterOpts())
+    _check_forward(scene_np, cam, gs.RasterOpts(), max_ambig_frac=TINY_BAND_FRAC)
 
 
 def test_forward_sh3_ragged_image():
@@ -270,7 +282,8 @@ def _check_backward(scene_np, cam, opts, g, tol=1e-3, max_ambig_frac=0.05):
     oo = oracle_opts(opts, cam)
     amb = oracle.render(scene_np, cam, oo)["ambig"]
     clean = (amb & AMBIG_IMAGE) == 0
-    assert clean.mean() >= 1.0 - max_ambig_frac, f"too many tie-band pixels: {1 - clean.mean():.3f}"
+    print(f"tie-band pixels (dL/dC zeroed) {int((~clean).sum())}/{clean.size} ({1 - clean.mean():.4%})")
+    assert clean.mean() >= 1.0 - max_ambig_frac, f"too many tie-band pixels: {1 - clean.mean():.4f}"
     g = g * clean[..., None]
     scene, ws, out, grads = run_forward_backward(scene_np, cam, opts, g)
     ref = oracle.backward(scene_np, cam, g.astype(np.float64), oo)
@@ -283,7 +296,7 @@ def _check_backward(scene_np, cam, opts, g, tol=1e-3, max_ambig_frac=0.05):
 def test_backward_tiny_scene_random_dLdC():
     scene_np, cam, _ = syn.tiny_scene_1k()
     g = syn.uniform_image(cam.height, cam.width, seed=41, lo=-1.0, hi=1.0)
-    _check_backward(scene_np, cam, gs.RasterOpts(), g)
+    _check_backward(scene_np, cam, gs.RasterOpts(), g, max_ambig_frac=TINY_BAND_FRAC)
 
 
 def test_backward_tiny_scene_l2_loss_path():
@@ -522,27 +535,62 @@ def test_loss_kernel(shape, offset):
 # Reduced-precision state (Sec. 3.3)
 # ---------------------------------------------------------------------------
 
+def paper_error_metrics(a, ref):
+    """The precision table's metrics (Sec. 4.6): RMSE over all gradient
+    elements, and the mean relative error |a - ref| / |ref| of the elements
+    whose reference magnitude lies in [10, inf), [0.1, 10) and [1e-3, 0.1)."""
+    a, ref = np.concatenate([x.ravel() for x in a]), np.concatenate([x.ravel() for x in ref])
+    out = {"rmse": float(np.sqrt(np.mean((a - ref) ** 2)))}
+    mag = np.abs(ref)
+    for name, lo, hi in (("mre_ge10", 10.0, np.inf), ("mre_0.1_10", 0.1, 10.0),
+                         ("mre_1e-3_0.1", 1e-3, 0.1)):
+        m = (mag >= lo) & (mag < hi)
+        out[name] = float(np.mean(np.abs(a[m] - ref[m]) / mag[m])) if m.any() else None
+    return out
+
+
 @pytest.mark.parametrize("fmt,img_tol,grad_tol", [("fp16", 2e-3, 1e-2), ("unorm16", 2e-3, 1e-2),
                                                   ("unorm8", 2.5e-3, 1e-1)])
 def test_reduced_precision_state(fmt, img_tol, grad_tol):
     """Stored colour against the unrounded FP64 oracle on the eight sweep views;
     gradients use the stored colour as C'_1.  unorm8 is the floor: its bound is
-    looser, and the measured error is printed."""
+    looser, and the measured error is printed.  Printed beside it: the same
+    errors of the oracle's emulation of the paper's render target, which rounds
+    (C, T) after every fragment (Sec. 3.3), and the paper's RMSE / MRE-bin
+    metrics of the stored-state gradients relative to the FP32-state ones."""
     scene_np, cams = syn.precision_sweep_views(8)
     opts = gs.RasterOpts(state_format=fmt)
+    opts32 = gs.RasterOpts(state_format="fp32")
     worst_img, worst = 0.0, {k: 0.0 for k in GROUPS}
+    emu_img, emu = 0.0, {k: 0.0 for k in GROUPS}
+    mine, full = [], []
     for i, cam in enumerate(cams):
         g = syn.uniform_image(cam.height, cam.width, seed=90 + i, lo=-1.0, hi=1.0)
         scene, ws, out, grads = run_forward_backward(scene_np, cam, opts, g)
+        _, _, _, grads32 = run_forward_backward(scene_np, cam, opts32, g)
         oo = oracle_opts(opts, cam)
         ref_img = oracle.render(scene_np, cam, oo)
         ok = (ref_img["ambig"] & AMBIG_IMAGE) == 0
+        assert 1.0 - ok.mean() <= TINY_BAND_FRAC, f"view {i}: tie-band pixels {1 - ok.mean():.4f}"
         st = gs.decode_state(out["state"], fmt).cpu().numpy().astype(np.float64)
         worst_img = max(worst_img, np.abs(st[..., :3] - ref_img["color"]).max(axis=2)[ok].max())
         ref = oracle.backward(scene_np, cam, g.astype(np.float64), oo)
         for k in GROUPS:
             worst[k] = max(worst[k], rel_l2(grads[k], ref[k]))
+        # the paper's per-fragment round trip, emulated by the oracle
+        oq = oracle_opts(opts, cam, quant=oracle.QUANT[fmt], per_fragment=True)
+        em_img = oracle.render(scene_np, cam, oq)["color"]
+        emu_img = max(emu_img, np.abs(em_img - ref_img["color"]).max(axis=2)[ok].max())
+        em = oracle.backward(scene_np, cam, g.astype(np.float64), oq, quant_cprime=True)
+        for k in GROUPS:
+            emu[k] = max(emu[k], rel_l2(em[k], ref[k]))
+        mine.append([grads[k] for k in GROUPS])
+        full.append([grads32[k] for k in GROUPS])
+    metrics = paper_error_metrics([x for v in mine for x in v], [x for v in full for x in v])
     print(f"{fmt}: stored-colour max-abs {worst_img:.2e}, gradient rel-L2 {worst}")
+    print(f"{fmt} per-fragment emulation (oracle): colour max-abs {emu_img:.2e}, "
+          f"gradient rel-L2 {emu}")
+    print(f"{fmt} vs FP32 state, paper metrics: {metrics}")
     assert worst_img <= img_tol
     for k in GROUPS:
         assert worst[k] <= grad_tol, f"{fmt} {k}: {worst[k]:.3e}"
