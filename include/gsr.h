@@ -66,13 +66,13 @@ enum {
 };
 
 /* Per-splat gradient reduction in the backward raster (Sec. 3.2).  The raster
- * kernels give each warp a footprint of 64 pixels (16x4) or, in blocks with
- * long splat lists, 32 (8x4) or 16 (4x4). */
+ * kernels give each warp a footprint of 64 pixels (8x8, two per lane) or, in
+ * blocks with long splat lists, 32 (8x4) or 16 (4x4). */
 enum {
-  GS_REDUCE_WARP = 0,    /* transpose-reduce over the warp: one vector-atomic triple per (splat,
-                            footprint) */
+  GS_REDUCE_WARP = 0,    /* summed over the warp first (in batches through shared memory): one
+                            set of vector atomics per (splat, footprint) */
   GS_REDUCE_NAIVE = 1,   /* one vector-atomic triple per lane that has a fragment (a lane's two
-                            pixels of a 16x4 band are added first) */
+                            pixels of an 8x8 footprint are added first) */
   GS_REDUCE_FRAGMENT = 2 /* one vector-atomic triple per fragment, every pixel its own (the
                             paper's 1x baseline of Sec. 4.3); front to back only */
 };
@@ -112,7 +112,7 @@ typedef struct gs_raster_opts {
   int32_t sh_degree;        /* 0..3 */
   float t_cull;             /* skip fragment i iff T_i < t_cull (Procedure 1); 0 disables */
   int32_t split_threshold;  /* a block whose splat list has at least this many entries is walked
-                               by eight warps (8x4 pixels, one per lane) instead of four (16x4,
+                               by eight warps (8x4 pixels, one per lane) instead of four (8x8,
                                two per lane), from 8x this many by sixteen half-warps (4x4);
                                0 = default (GS_SPLIT_THRESHOLD_DEFAULT).  Results do not depend
                                on it. */

@@ -327,7 +327,7 @@ __device__ __forceinline__ int length_bucket(uint32_t len) {
 }
 
 // Raster work items, longest lists first: a counting sort of the blocks by
-// length bucket, each block writing its items contiguously: four 16x4 bands,
+// length bucket, each block writing its items contiguously: four 8x8 quadrants,
 // eight 8x4 cells when its list has at least `split` entries, sixteen 4x4
 // cells from 8 `split` entries on (raster.cu has the encoding).  The item
 // count goes to the header.
