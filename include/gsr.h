@@ -262,6 +262,48 @@ int gs_zero_touched_gradients(gs_workspace* ws, int32_t n, float* d_means, float
                               float* d_quats, float* d_opacities, float* d_sh,
                               gs_stream_t stream);
 
+/* Depth slabs (Sec. 2.1.2: front-to-back blending is associative over
+ * contiguous runs of the depth order).  After gs_project and gs_sort, slab k of
+ * n_slabs is the run of depth ranks [k V / n_slabs, (k + 1) V / n_slabs) of
+ * the V visible splats (V is read on the device).  gs_raster_forward_slab bins
+ * and blends that run alone, each pixel starting from T = 1, and writes its
+ * colour C_k (image, may be null), state (C_k, T_k) in opts->state_format,
+ * last rank (a global depth rank) and fragment count (may be null).  T-culling
+ * (opts->t_cull) uses the slab's own transmittance, so slabs composite to the
+ * single-pass image exactly when t_cull = 0.  The whole view's pairs may
+ * exceed the workspace's pair capacity as long as one slab's fit (else the
+ * device status reads GS_ERR_CAPACITY).  Not with the memory-efficiency mode.
+ * Slabs can be rendered on different GPUs, each with a replica of the scene:
+ * the exchange is one gather of the states, then gs_slab_composite. */
+int gs_raster_forward_slab(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                           int32_t slab, int32_t n_slabs, float* image, void* state,
+                           uint32_t* last, uint32_t* n_contrib, gs_stream_t stream);
+
+/* "Over" composite of n_slabs slab states laid out one after another,
+ * states[k][npix] in state_format (16, 8, 8 or 4 bytes per pixel, the format's
+ * layout): image [npix][3] = C_0 + T_0 (C_1 + T_1 (C_2 + ...)), trans [npix] =
+ * T_0 T_1 ..., and for the backward of each slab t_front [n_slabs][npix] =
+ * T_0 ... T_{k-1} and behind [n_slabs][npix][3] = the composite of the slabs
+ * after k (0 for the last).  Any output may be null.  Device pointers. */
+int gs_slab_composite(const void* states, int32_t state_format, int32_t n_slabs, int64_t npix,
+                      float* image, float* trans, float* t_front, float* behind,
+                      gs_stream_t stream);
+
+/* Backward of slab k (after gs_raster_forward_slab of that slab on ws, same
+ * scene, camera and opts): Procedure 1 over the slab's fragments with the
+ * image gradient dL_dimage [H][W][3] scaled by t_front (slab k's [H][W] of
+ * gs_slab_composite; null = 1) and C' starting from the slab's colour plus T_k
+ * times behind (slab k's [H][W][3]; null = 0), then the chain rule; gradients
+ * are ADDED to d_*, so the slabs' calls sum to the single-pass gradient (at
+ * t_cull = 0).  Arguments otherwise as gs_raster_backward. */
+int gs_raster_backward_slab(gs_workspace* ws, const float* means, const float* scales,
+                            const float* quats, const float* opacities, const float* sh,
+                            int32_t n, const gs_camera* cam, const gs_raster_opts* opts,
+                            int32_t slab, int32_t n_slabs, const void* state, const uint32_t* last,
+                            const float* t_front, const float* behind, const float* dL_dimage,
+                            float* d_means, float* d_scales, float* d_quats, float* d_opacities,
+                            float* d_sh, gs_stream_t stream);
+
 /* Summed image loss over n_values floats: L1 = sum |image - target| (dL/dimage =
  * sign) or L2 = sum (image - target)^2 (dL/dimage = 2 (image - target)).
  * Writes dL_dimage (may be null) and *loss (one device double). */

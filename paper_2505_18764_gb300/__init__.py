@@ -318,6 +318,76 @@ def raster_backward(ws: Workspace, scene: SceneTensors, cam, opts: RasterOpts, s
     return grads
 
 
+def raster_forward_slab(ws: Workspace, cam, opts: RasterOpts, slab: int, n_slabs: int,
+                        image=None, state=None, last=None, n_contrib=None, want_image=True,
+                        want_n_contrib=False, stream=None):
+    """Bins and blends depth slab `slab` of `n_slabs` alone (each pixel from
+    T = 1): its colour C_k, state (C_k, T_k), last rank and count."""
+    H, W = int(cam.height), int(cam.width)
+    dev = ws.device
+    if image is None and want_image:
+        image = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    if state is None:
+        state = alloc_state(H, W, opts.state_format, dev)
+    if last is None:
+        last = torch.empty((H, W), dtype=torch.int32, device=dev)
+    if n_contrib is None and want_n_contrib:
+        n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    _check_image_buffers(cam, opts.state_format, image, state, last, n_contrib)
+    check(_lib.load().gs_raster_forward_slab(ws.ref, ctypes.byref(camera_to_c(cam)),
+                                             ctypes.byref(opts.to_c()), int(slab), int(n_slabs),
+                                             _f32(image, "image"), _ptr(state, "state"),
+                                             _ptr(last, "last"), _ptr(n_contrib, "n_contrib"),
+                                             _stream(stream)),
+          "gs_raster_forward_slab")
+    return dict(image=image, state=state, last=last, n_contrib=n_contrib)
+
+
+def slab_composite(states: torch.Tensor, fmt: str, want_backward=True, stream=None) -> dict:
+    """"Over" composite of slab states [n, H, W, bytes]: image [H, W, 3], trans
+    [H, W] and, for the slabs' backward, t_front [n, H, W] and behind
+    [n, H, W, 3]."""
+    n, H, W = int(states.shape[0]), int(states.shape[1]), int(states.shape[2])
+    if tuple(states.shape[3:]) != (STATE_BYTES[fmt],) or states.dtype != torch.uint8:
+        raise ValueError(f"states must be uint8 [n, H, W, {STATE_BYTES[fmt]}]")
+    dev = states.device
+    image = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    trans = torch.empty((H, W), dtype=torch.float32, device=dev)
+    t_front = torch.empty((n, H, W), dtype=torch.float32, device=dev) if want_backward else None
+    behind = torch.empty((n, H, W, 3), dtype=torch.float32, device=dev) if want_backward else None
+    check(_lib.load().gs_slab_composite(_ptr(states, "states"), STATE_FORMATS[fmt], n, H * W,
+                                        _f32(image, "image"), _f32(trans, "trans"),
+                                        _f32(t_front, "t_front"), _f32(behind, "behind"),
+                                        _stream(stream)), "gs_slab_composite")
+    return dict(image=image, trans=trans, t_front=t_front, behind=behind)
+
+
+def raster_backward_slab(ws: Workspace, scene: SceneTensors, cam, opts: RasterOpts, slab: int,
+                         n_slabs: int, state, last, dL_dimage, t_front=None, behind=None,
+                         grads: dict | None = None, stream=None) -> dict:
+    """Backward of one depth slab (after raster_forward_slab of that slab on ws):
+    image gradient scaled by t_front [H, W], C' seeded with the slab's colour
+    plus T_slab * behind [H, W, 3]; gradients added to `grads`."""
+    if grads is None:
+        grads = zero_grads(scene)
+    _check_scene(scene, opts.sh_degree)
+    _check_grads(scene, grads)
+    _check_image_buffers(cam, opts.state_format, None, state, last, None, dL_dimage)
+    H, W = int(cam.height), int(cam.width)
+    _need(t_front, H * W, "t_front")
+    _need(behind, H * W * 3, "behind")
+    m, s, q, o, sh = scene.tensors()
+    check(_lib.load().gs_raster_backward_slab(
+        ws.ref, _f32(m, "means"), _f32(s, "scales"), _f32(q, "quats"), _f32(o, "opacities"),
+        _f32(sh, "sh"), scene.n, ctypes.byref(camera_to_c(cam)), ctypes.byref(opts.to_c()),
+        int(slab), int(n_slabs), _ptr(state, "state"), _ptr(last, "last"),
+        _f32(t_front, "t_front"), _f32(behind, "behind"), _f32(dL_dimage, "dL_dimage"),
+        _f32(grads["means"], "d_means"), _f32(grads["scales"], "d_scales"),
+        _f32(grads["quats"], "d_quats"), _f32(grads["opacities"], "d_opacities"),
+        _f32(grads["sh"], "d_sh"), _stream(stream)), "gs_raster_backward_slab")
+    return grads
+
+
 def zero_touched_gradients(ws: Workspace, grads: dict, stream=None) -> dict:
     """Zeroes the gradient rows of the splats the last sort on ws ordered (the
     rows a backward on that view adds to); buffers that were all zero before
@@ -519,4 +589,5 @@ __all__ = ["RasterOpts", "SceneTensors", "Workspace", "project", "sort", "raster
            "blend_forward", "blend_backward", "project_backward",
            "raster_backward", "loss", "render", "render_batch", "Request", "check_status",
            "read_counters", "fp32_fma_rate", "copy_array", "sort_pairs", "sort_pairs_noalloc", "sort_pairs_noalloc_status", "stalled_sort_selftest", "decode_state", "alloc_state",
-           "camera_to_c", "GsError", "zero_grads", "NONE_RANK"]
+           "camera_to_c", "GsError", "zero_grads", "NONE_RANK", "raster_forward_slab",
+           "slab_composite", "raster_backward_slab"]

@@ -101,6 +101,15 @@ _SIGS = {
     "gs_test_stalled_sort": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                              c_uint32, c_void_p],
     "gs_fp32_fma_rate": [c_int32, POINTER(c_double), c_void_p],
+    "gs_raster_forward_slab": [POINTER(GsWorkspace), POINTER(GsCamera), POINTER(GsRasterOpts),
+                               c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p],
+    "gs_raster_backward_slab": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_int32, POINTER(GsCamera), POINTER(GsRasterOpts),
+                                c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p],
+    "gs_slab_composite": [c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                          c_void_p, c_void_p],
     "gs_zero_touched_gradients": [POINTER(GsWorkspace), c_int32, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p],
 }

@@ -46,7 +46,10 @@ cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint
 cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, uint32_t*,
                               const Header*, uint32_t*, const uint32_t*, const SplatRec*, int, int,
                               int, int, float, int, const void*, const uint32_t*, const float*,
-                              float*, int, int, int, float4*, int, int, int, cudaStream_t);
+                              float*, int, int, int, float4*, int, int, const float*,
+                              const float*, int, cudaStream_t);
+cudaError_t launch_slab_composite(const void*, int, int, int64_t, float*, float*, float*, float*,
+                                  int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
                         cudaStream_t);
 size_t sort_tiles(size_t n);
@@ -340,7 +343,9 @@ static int check_bound(gs_workspace* ws, const gs_camera* cam, const gs_raster_o
 namespace {
 
 // Binning, first pass: records into depth order, box pair counts, their scan.
-int bin_count_stage(gs_workspace* ws, cudaStream_t st) {
+// skip_capacity: the whole view's pairs may exceed the capacity (the
+// memory-efficiency mode and depth slabs bin part of the view at a time).
+int bin_count_stage(gs_workspace* ws, cudaStream_t st, int skip_capacity = -1) {
   Header* hdr = at<Header>(ws, L_HDR);
   const int grid_cap = num_sms() * kPersistentPerSm;
   GS_CUDA(cudaMemsetAsync(&hdr->tile_counter[8], 0, sizeof(uint32_t), st), "bin counter");
@@ -348,16 +353,18 @@ int bin_count_stage(gs_workspace* ws, cudaStream_t st) {
                            at<uint2>(ws, L_BOXES_ID), at<SplatRec>(ws, L_REC_SORTED),
                            at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN),
                            at<uint32_t>(ws, L_EPOCH), at<uint32_t>(ws, L_OFFSETS),
-                           at<uint2>(ws, L_BOXES), (uint32_t)ws->pair_cap, ws->chunked, ws->n,
-                           grid_cap, st),
+                           at<uint2>(ws, L_BOXES), (uint32_t)ws->pair_cap,
+                           skip_capacity >= 0 ? skip_capacity : ws->chunked, ws->n, grid_cap, st),
           "bin count kernel");
   return GS_OK;
 }
 
 // Binning of chunk k (the only chunk without the memory-efficiency mode):
 // emission, the pair sort by block, block ranges and raster work items.
+// mode: 0 the whole view, 1 the memory-efficiency mode's chunk k of pair
+// budget B, 2 depth slab k of B (chunk_setup_kernel, bin.cu).
 int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
-                    uint32_t k, uint32_t B, cudaStream_t st) {
+                    uint32_t k, uint32_t B, cudaStream_t st, int mode = -1) {
   Header* hdr = at<Header>(ws, L_HDR);
   uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
   int gw, gh;
@@ -365,7 +372,8 @@ int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts
   const int grid_cap = num_sms() * kPersistentPerSm;
   GS_CUDA(launch_bin_chunk(at<uint32_t>(ws, L_OFFSETS), at<uint2>(ws, L_BOXES),
                            at<SplatRec>(ws, L_REC_SORTED), hdr, epoch, k, B, (uint32_t)ws->pair_cap,
-                           ws->chunked, at<uint2>(ws, L_RANGES), at<uint32_t>(ws, L_PKA),
+                           mode >= 0 ? mode : ws->chunked, at<uint2>(ws, L_RANGES),
+                           at<uint32_t>(ws, L_PKA),
                            at<uint32_t>(ws, L_PVA), gw, gh, ws->pair_passes, grid_cap, st),
           "bin emit kernel");
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
@@ -430,7 +438,8 @@ int raster_fwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
 
 int raster_bwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
                      const void* state, const uint32_t* last, const float* dL_dimage,
-                     int chunk_in, int chunk_out, cudaStream_t st) {
+                     int chunk_in, int chunk_out, cudaStream_t st,
+                     const float* t_front = nullptr, const float* behind = nullptr) {
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
@@ -444,7 +453,7 @@ int raster_bwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
                             opts->reduce_threshold > 0 ? opts->reduce_threshold
                                                        : GS_REDUCE_THRESHOLD_DEFAULT,
                             opts->backward_order, at<float4>(ws, L_CHUNK_STATE), chunk_in,
-                            chunk_out, num_sms(), st),
+                            chunk_out, t_front, behind, num_sms(), st),
           "raster backward kernel");
   return GS_OK;
 }
@@ -586,6 +595,62 @@ int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales
   if (rc) return rc;
   return gs_project_backward(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
                              d_scales, d_quats, d_opacities, d_sh, stream);
+}
+
+int gs_raster_forward_slab(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                           int32_t slab, int32_t n_slabs, float* image, void* state,
+                           uint32_t* last, uint32_t* n_contrib, gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (ws->chunked) return fail(GS_ERR_INVALID_ARG, "depth slabs do not combine with the memory-efficiency mode");
+  if (n_slabs < 1 || slab < 0 || slab >= n_slabs)
+    return fail(GS_ERR_INVALID_ARG, "slab %d of %d is out of range", slab, n_slabs);
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last)) return fail(GS_ERR_INVALID_ARG, "state and last are required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  rc = bin_count_stage(ws, st, 1);
+  if (!rc) rc = bin_chunk_stage(ws, cam, opts, (uint32_t)slab, (uint32_t)n_slabs, st, 2);
+  if (!rc) rc = raster_fwd_stage(ws, cam, opts, image, state, last, n_contrib, 0, st);
+  return rc;
+}
+
+int gs_raster_backward_slab(gs_workspace* ws, const float* means, const float* scales,
+                            const float* quats, const float* opacities, const float* sh,
+                            int32_t n, const gs_camera* cam, const gs_raster_opts* opts,
+                            int32_t slab, int32_t n_slabs, const void* state, const uint32_t* last,
+                            const float* t_front, const float* behind, const float* dL_dimage,
+                            float* d_means, float* d_scales, float* d_quats, float* d_opacities,
+                            float* d_sh, gs_stream_t stream) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (ws->chunked) return fail(GS_ERR_INVALID_ARG, "depth slabs do not combine with the memory-efficiency mode");
+  if (n_slabs < 1 || slab < 0 || slab >= n_slabs)
+    return fail(GS_ERR_INVALID_ARG, "slab %d of %d is out of range", slab, n_slabs);
+  if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
+  if (n > 0 && (!means || !scales || !quats || !opacities || !sh || !d_means || !d_scales ||
+                !d_quats || !d_opacities || !d_sh))
+    return fail(GS_ERR_INVALID_ARG, "null parameter or gradient pointer");
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last || !dL_dimage))
+    return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
+  rc = raster_bwd_stage(ws, cam, opts, state, last, dL_dimage, 0, 0,
+                        reinterpret_cast<cudaStream_t>(stream), t_front, behind);
+  if (rc) return rc;
+  return gs_project_backward(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
+                             d_scales, d_quats, d_opacities, d_sh, stream);
+}
+
+int gs_slab_composite(const void* states, int32_t state_format, int32_t n_slabs, int64_t npix,
+                      float* image, float* trans, float* t_front, float* behind,
+                      gs_stream_t stream) {
+  if (state_format < 0 || state_format > 3) return fail(GS_ERR_INVALID_ARG, "bad state_format %d", state_format);
+  if (n_slabs < 1) return fail(GS_ERR_INVALID_ARG, "n_slabs must be >= 1");
+  if (npix < 0) return fail(GS_ERR_INVALID_ARG, "negative npix");
+  if (npix > 0 && !states) return fail(GS_ERR_INVALID_ARG, "states is null");
+  GS_CUDA(launch_slab_composite(states, state_format, n_slabs, npix, image, trans, t_front, behind,
+                                num_sms(), reinterpret_cast<cudaStream_t>(stream)),
+          "slab composite kernel");
+  return GS_OK;
 }
 
 int gs_loss(const float* image, const float* target, int64_t n_values, int32_t kind,

@@ -32,6 +32,7 @@ constexpr unsigned long long kBinAgg = 1ull << 30;
 constexpr unsigned long long kBinPre = 2ull << 30;
 constexpr unsigned long long kBinCount = (1ull << 30) - 1;
 constexpr int kEmitChunk = 2048;  // pairs written per CTA step of the emission pass
+constexpr int kChunkWhole = 0, kChunkBudget = 1, kChunkSlab = 2;   // chunk_setup_kernel modes
 
 // Pass 1: one tile of 1024 depth ranks per step of a persistent loop.
 __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
@@ -191,20 +192,33 @@ __device__ __forceinline__ uint32_t warp_rank_of_pair(const uint32_t* __restrict
 }
 
 // Chunk k of the view: pair indices [pair_base, pair_base + pairs) and the
-// per-chunk state the emission and the pair sort start from.  Without the
-// memory-efficiency mode there is one chunk, the first `capacity` pairs.  It
-// also advances the epoch: the pair sort's look-back words of any earlier
-// chunk or binning then carry a stale tag and are never taken for this one's.
+// per-chunk state the emission and the pair sort start from.  mode
+// kChunkWhole: one chunk, the first `capacity` pairs; kChunkBudget (the
+// memory-efficiency mode): the splats whose first pair index lies in
+// [k B, (k + 1) B); kChunkSlab: depth slab k of B, the ranks
+// [k V / B, (k + 1) V / B) (a slab whose pairs exceed the capacity records
+// kStatusCapacity and keeps the first `capacity`).  It also advances the
+// epoch: the pair sort's look-back words of any earlier chunk or binning then
+// carry a stale tag and are never taken for this one's.
 __global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __restrict__ offsets,
                                                           Header* __restrict__ hdr,
                                                           uint32_t* __restrict__ epoch, uint32_t k,
                                                           uint32_t B, uint32_t pair_cap,
-                                                          int chunked, uint2* __restrict__ ranges,
+                                                          int mode, uint2* __restrict__ ranges,
                                                           int nblocks) {
   const uint32_t V = hdr->visible, total = hdr->pairs_wanted;
   if (threadIdx.x == 0) {
     uint32_t lo = 0, hi = min(total, pair_cap);
-    if (chunked) {
+    if (mode == kChunkSlab) {
+      const uint32_t r0 = (uint32_t)((unsigned long long)k * V / B);
+      const uint32_t r1 = (uint32_t)((unsigned long long)(k + 1) * V / B);
+      lo = r0 < V ? offsets[r0] : total;
+      hi = r1 < V ? offsets[r1] : total;
+      if (hi - lo > pair_cap) {
+        atomicOr(&hdr->status, kStatusCapacity);
+        hi = lo + pair_cap;
+      }
+    } else if (mode == kChunkBudget) {
       // first rank whose first pair index is >= t
       auto first_at = [&](unsigned long long t) -> uint32_t {
         if (t >= total) return total;
@@ -421,10 +435,10 @@ cudaError_t launch_bin_count(const uint32_t* sorted_ids, const SplatRec* rec,
 cudaError_t launch_bin_chunk(const uint32_t* offsets, const uint2* boxes,
                              const SplatRec* rec_sorted, Header* hdr, uint32_t* epoch, uint32_t k,
                              uint32_t B,
-                             uint32_t pair_cap, int chunked, uint2* ranges, uint32_t* pair_keys,
+                             uint32_t pair_cap, int mode, uint2* ranges, uint32_t* pair_keys,
                              uint32_t* pair_vals, int gw, int gh, int pair_passes, int grid_cap,
                              cudaStream_t st) {
-  chunk_setup_kernel<<<1, 256, 0, st>>>(offsets, hdr, epoch, k, B, pair_cap, chunked, ranges,
+  chunk_setup_kernel<<<1, 256, 0, st>>>(offsets, hdr, epoch, k, B, pair_cap, mode, ranges,
                                         gw * gh);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

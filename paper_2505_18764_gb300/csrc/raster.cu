@@ -406,12 +406,25 @@ struct PixelBwd {
   uint32_t end;             // depth rank after the pixel's last fragment
 };
 
-// chunk_state (memory-efficiency mode): with chunk_in, (D, T) continue from the
-// previous chunk instead of (g . stored C, 1).
+// Per-pixel inputs of the backward beyond the state: chunk_state (memory-
+// efficiency mode: with chunk_in, (D, T) continue from the previous chunk
+// instead of (g . stored C, 1)) and, for a depth slab, t_front (the
+// transmittance of the slabs in front: the slab's colour enters the image as
+// t_front C_slab, so its image gradient is t_front g) and behind (the colour
+// composited from the slabs behind: the colour seen from the slab's start is
+// C_slab + T_slab behind, which is where C' starts).  Null pointers stand for
+// t_front = 1 and behind = 0.
+struct BwdExtra {
+  const float4* chunk_state;
+  int chunk_in;
+  const float* t_front;
+  const float* behind;
+};
+
 __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, int y, int W,
                                                int fmt, const void* state,
                                                const uint32_t* last_in, const float* dLdC,
-                                               const float4* chunk_state, int chunk_in) {
+                                               const BwdExtra& ex) {
   p.D = 0.f;
   p.g0 = p.g1 = p.g2 = 0.f;
   p.T = 1.f;
@@ -419,12 +432,21 @@ __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, i
   if (valid) {
     const size_t pix = (size_t)y * W + x;
     p.g0 = dLdC[3 * pix]; p.g1 = dLdC[3 * pix + 1]; p.g2 = dLdC[3 * pix + 2];
-    if (chunk_in) {
-      const float4 cs = chunk_state[pix];
+    if (ex.t_front) {
+      const float tf = ex.t_front[pix];
+      p.g0 *= tf; p.g1 *= tf; p.g2 *= tf;
+    }
+    if (ex.chunk_in) {
+      const float4 cs = ex.chunk_state[pix];
       p.D = cs.x;
       p.T = cs.y;
     } else {
-      const float4 st = load_state(state, fmt, pix);
+      float4 st = load_state(state, fmt, pix);
+      if (ex.behind) {
+        st.x = fmaf(st.w, ex.behind[3 * pix], st.x);
+        st.y = fmaf(st.w, ex.behind[3 * pix + 1], st.y);
+        st.z = fmaf(st.w, ex.behind[3 * pix + 2], st.z);
+      }
       p.D = p.g0 * st.x + p.g1 * st.y + p.g2 * st.z;
     }
     const uint32_t l = last_in[pix];
@@ -478,7 +500,7 @@ __device__ __forceinline__ void bwd_item(BwdRing& R, GradBatch& B,
                                          int x0, int y0, int lane, int W, int H, int fmt,
                                          const void* state, const uint32_t* last_in,
                                          const float* dLdC, float* g2d, int threshold,
-                                         float4* chunk_state, int chunk_in, int chunk_out) {
+                                         const BwdExtra& ex, float4* chunk_state, int chunk_out) {
   int x, ya;
   bool own;
   lane_pixels<COLS>(x0, y0, lane, x, ya, own);
@@ -486,7 +508,7 @@ __device__ __forceinline__ void bwd_item(BwdRing& R, GradBatch& B,
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
   PixelBwd pa;
   const bool va = own && x < W && ya < H;
-  load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
+  load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, ex);
   // depth ranks >= this contribute nowhere in the footprint
   const uint32_t warp_end = __reduce_max_sync(kFull, pa.end);
 
@@ -608,8 +630,8 @@ __device__ __forceinline__ void bwd_item_pair(BwdRing& R, GradBatch& B,
                                               uint2 range, int x0, int y0, int lane, int W,
                                               int H, int fmt, const void* state,
                                               const uint32_t* last_in, const float* dLdC,
-                                              float* g2d, int threshold, float4* chunk_state,
-                                              int chunk_in, int chunk_out) {
+                                              float* g2d, int threshold, const BwdExtra& ex,
+                                              float4* chunk_state, int chunk_out) {
   int x, ya;
   bool own;
   lane_pixels<16>(x0, y0, lane, x, ya, own);
@@ -621,8 +643,8 @@ __device__ __forceinline__ void bwd_item_pair(BwdRing& R, GradBatch& B,
   PairBwd pp;
   {
     PixelBwd pa, pb;
-    load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
-    load_pixel_bwd(pb, vb, x, yb, W, fmt, state, last_in, dLdC, chunk_state, chunk_in);
+    load_pixel_bwd(pa, va, x, ya, W, fmt, state, last_in, dLdC, ex);
+    load_pixel_bwd(pb, vb, x, yb, W, fmt, state, last_in, dLdC, ex);
     pp = pack_pair(pa, pb);
   }
   // depth ranks >= this contribute nowhere in the footprint
@@ -699,9 +721,12 @@ struct PixelBack {
   uint32_t end;
 };
 
+// A depth slab (see BwdExtra) starts S at the colour behind the slab's last
+// fragment, T_slab behind, and scales g by t_front.
 __device__ __forceinline__ void load_pixel_back(PixelBack& p, bool valid, int x, int y, int W,
                                                 int fmt, const void* state,
-                                                const uint32_t* last_in, const float* dLdC) {
+                                                const uint32_t* last_in, const float* dLdC,
+                                                const BwdExtra& ex) {
   p.S0 = p.S1 = p.S2 = 0.f;
   p.g0 = p.g1 = p.g2 = 0.f;
   p.T = 1.f;
@@ -710,6 +735,15 @@ __device__ __forceinline__ void load_pixel_back(PixelBack& p, bool valid, int x,
     const size_t pix = (size_t)y * W + x;
     p.T = load_state(state, fmt, pix).w;
     p.g0 = dLdC[3 * pix]; p.g1 = dLdC[3 * pix + 1]; p.g2 = dLdC[3 * pix + 2];
+    if (ex.t_front) {
+      const float tf = ex.t_front[pix];
+      p.g0 *= tf; p.g1 *= tf; p.g2 *= tf;
+    }
+    if (ex.behind) {
+      p.S0 = p.T * ex.behind[3 * pix];
+      p.S1 = p.T * ex.behind[3 * pix + 1];
+      p.S2 = p.T * ex.behind[3 * pix + 2];
+    }
     const uint32_t l = last_in[pix];
     p.end = (l == kNone) ? 0u : l + 1u;
   }
@@ -786,7 +820,7 @@ __device__ __forceinline__ void bwd_item_back(BwdRing& R, GradBatch& B,
                                               uint2 range, int x0, int y0, int lane, int W, int H,
                                               int fmt, const void* state,
                                               const uint32_t* last_in, const float* dLdC,
-                                              float* g2d, int threshold) {
+                                              float* g2d, int threshold, const BwdExtra& ex) {
   constexpr int NPX = COLS == 16 ? 2 : 1;
   int x, ya;
   bool own;
@@ -795,9 +829,9 @@ __device__ __forceinline__ void bwd_item_back(BwdRing& R, GradBatch& B,
   const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
   const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
   PixelBack pa, pb;
-  load_pixel_back(pa, own && x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC);
+  load_pixel_back(pa, own && x < W && ya < H, x, ya, W, fmt, state, last_in, dLdC, ex);
   if (NPX == 2) {
-    load_pixel_back(pb, x < W && yb < H, x, yb, W, fmt, state, last_in, dLdC);
+    load_pixel_back(pb, x < W && yb < H, x, yb, W, fmt, state, last_in, dLdC, ex);
   } else {
     pb.S0 = pb.S1 = pb.S2 = 0.f;
     pb.g0 = pb.g1 = pb.g2 = 0.f;
@@ -868,8 +902,10 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, const void* __restrict__ state, const uint32_t* __restrict__ last_in,
     const float* __restrict__ dLdC, float* __restrict__ g2d, int threshold, int back,
-    float4* __restrict__ chunk_state, int chunk_in, int chunk_out) {
+    float4* __restrict__ chunk_state, int chunk_in, int chunk_out,
+    const float* __restrict__ t_front, const float* __restrict__ behind) {
   __shared__ BwdRing rings[kWarps];
+  const BwdExtra ex{chunk_state, chunk_in, t_front, behind};
   __shared__ GradBatch batches[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   BwdRing& R = rings[warp];
@@ -882,24 +918,24 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     if (back) {
       if (cols == 16)
         bwd_item_back<16, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                                last_in, dLdC, g2d, threshold);
+                                last_in, dLdC, g2d, threshold, ex);
       else if (cols == 8)
         bwd_item_back<8, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                               last_in, dLdC, g2d, threshold);
+                               last_in, dLdC, g2d, threshold, ex);
       else
         bwd_item_back<4, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                               last_in, dLdC, g2d, threshold);
+                               last_in, dLdC, g2d, threshold, ex);
       continue;
     }
     if (cols == 16)
       bwd_item_pair<MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                          last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
+                          last_in, dLdC, g2d, threshold, ex, chunk_state, chunk_out);
     else if (cols == 8)
       bwd_item<8, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                        last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
+                        last_in, dLdC, g2d, threshold, ex, chunk_state, chunk_out);
     else
       bwd_item<4, MODE>(R, B, rec, pair_ranks, range, x0, y0, lane, W, H, fmt, state,
-                        last_in, dLdC, g2d, threshold, chunk_state, chunk_in, chunk_out);
+                        last_in, dLdC, g2d, threshold, ex, chunk_state, chunk_out);
   }
 }
 
@@ -1002,7 +1038,8 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
                               int W, int H, int gw, int gh, float t_cull, int fmt,
                               const void* state, const uint32_t* last, const float* dLdC,
                               float* g2d, int mode, int threshold, int back, float4* chunk_state,
-                              int chunk_in, int chunk_out, int num_sms, cudaStream_t st) {
+                              int chunk_in, int chunk_out, const float* t_front,
+                              const float* behind, int num_sms, cudaStream_t st) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
@@ -1014,19 +1051,19 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_NAIVE><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold, back, chunk_state, chunk_in, chunk_out);
+        threshold, back, chunk_state, chunk_in, chunk_out, t_front, behind);
   } else if (mode == GS_REDUCE_FRAGMENT) {
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_FRAGMENT>);
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_FRAGMENT><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold, back, chunk_state, chunk_in, chunk_out);
+        threshold, back, chunk_state, chunk_in, chunk_out, t_front, behind);
   } else {
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_WARP>);
     const int grid = per_sm * num_sms;
     raster_bwd_kernel<GS_REDUCE_WARP><<<grid, kThreads, 0, st>>>(
         ranges, items, hdr, next, pair_ranks, rec, W, H, gw, t_cull, fmt, state, last, dLdC, g2d,
-        threshold, back, chunk_state, chunk_in, chunk_out);
+        threshold, back, chunk_state, chunk_in, chunk_out, t_front, behind);
   }
   return cudaGetLastError();
 }
