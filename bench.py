@@ -414,8 +414,13 @@ def run_chunked(args, gs, torch, scene, ccam, target, dev, stream, caps=(1 << 20
     count and workspace bytes against the default single-pass workspace."""
     W, H = ccam.width, ccam.height
     o_def = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4)
+    ws_def = gs.Workspace(scene.n, W, H, o_def, device=dev)
+    sb = ws_def.sort_bytes()
     out = dict(default_workspace_bytes=gs.Workspace.required_bytes(scene.n, W, H, o_def),
-               default_pair_capacity=max(16 * scene.n, 1 << 22), runs=[])
+               default_pair_capacity=max(16 * scene.n, 1 << 22),
+               default_sort_bytes=sb["depth_sort"] + sb["pair_sort"],
+               default_sort_bytes_split=sb, runs=[])
+    del ws_def
     grads = gs.zero_grads(scene)
     for cap in caps:
         o = gs.RasterOpts(state_format="fp32", sh_degree=3, t_cull=1e-4, chunked=True,
@@ -444,8 +449,10 @@ def run_chunked(args, gs, torch, scene, ccam, target, dev, stream, caps=(1 << 20
         b.record(stream)
         torch.cuda.synchronize(dev)
         gs.check_status(ws, stream)
+        sb = ws.sort_bytes()
         out["runs"].append(dict(pair_capacity=cap, chunks=int(ws.c.n_chunks),
                                 workspace_bytes=int(ws.nbytes),
+                                sort_bytes=sb["depth_sort"] + sb["pair_sort"], sort_bytes_split=sb,
                                 pair_buffer_bytes=4 * 4 * cap,
                                 ms_per_view=round(a.elapsed_time(b) / K, 4)))
         del ws
@@ -631,7 +638,7 @@ def run_serving(args, dev):
     def cam_for(s):
         return syn.orbit_camera(s["angle"], 4.0, 60.0, s["width"], s["height"])
 
-    ex = CudaExecutor(scenes, n_slots=8)
+    ex = CudaExecutor(scenes, n_slots=8, reuse_outputs=True)
     # warm-up (untimed): every (scene, resolution, mode) once, which also sizes
     # the pair capacity of each combination
     combos = [dict(arrival=0.0, scene=si, width=w, height=h, backward=b, angle=0.3 * si + 0.1 * ri)
@@ -641,7 +648,12 @@ def run_serving(args, dev):
     Server(ex, hbm_budget_bytes=120 << 30, max_slots=8).run(warm, realtime=False, keep_results=False)
     reqs = make_requests(specs, cam_for)
     srv = Server(ex, hbm_budget_bytes=120 << 30, max_slots=8)
+    ex.gpu_ms.clear()
     stats = srv.run(reqs, realtime=True, keep_results=False)
+    stats["gpu_ms_per_request_mean"] = float(np.mean(ex.gpu_ms)) if ex.gpu_ms else None
+    # sum of the requests' device spans over the wall time (streams overlap, so
+    # above 1 means several requests were on the GPU at once)
+    stats["device_span_share"] = float(np.sum(ex.gpu_ms) / (stats["wall_s"] * 1e3))
     fwd = [r.latency for r in reqs if r.status == "done" and not r.backward]
     bwd = [r.latency for r in reqs if r.status == "done" and r.backward]
     stats["p99_fwd_ms"] = float(np.percentile(fwd, 99) * 1e3) if fwd else None

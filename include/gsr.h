@@ -332,6 +332,12 @@ int gs_render_batch_graph(const gs_request* reqs, int32_t n, gs_workspace* ws,
  * before freeing a workspace's memory that will not be used again. */
 int gs_graph_release(gs_workspace* ws);
 
+/* Sorting memory of a workspace (the paper's memory table, Sec. 4.5, counts
+ * it apart): *depth_sort = the depth keys, the key/value ping-pong buffers and
+ * the radix passes' look-back words; *pair_sort = the (block, rank) pair
+ * buffers sized by the pair capacity.  Host outputs. */
+int gs_workspace_sort_bytes(const gs_workspace* ws, size_t* depth_sort, size_t* pair_sort);
+
 /* Synchronises `stream` and returns the device status recorded in `ws`
  * (GS_OK, GS_ERR_CAPACITY or GS_ERR_TIMEOUT). */
 int gs_check_status(gs_workspace* ws, gs_stream_t stream);

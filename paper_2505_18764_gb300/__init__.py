@@ -183,6 +183,13 @@ class Workspace:
     def ref(self):
         return ctypes.byref(self.c)
 
+    def sort_bytes(self) -> dict:
+        """Sorting memory: depth-sort buffers and look-back words, pair buffers."""
+        d, p = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        check(_lib.load().gs_workspace_sort_bytes(self.ref, ctypes.byref(d), ctypes.byref(p)),
+              "gs_workspace_sort_bytes")
+        return dict(depth_sort=int(d.value), pair_sort=int(p.value))
+
     def release_graph(self):
         """Frees the CUDA graph render_batch(graph=True) keeps for this workspace."""
         lib = _lib._lib

@@ -92,6 +92,7 @@ _SIGS = {
     "gs_render_batch_graph": [POINTER(GsRequest), c_int32, POINTER(GsWorkspace), c_void_p],
     "gs_graph_release": [POINTER(GsWorkspace)],
     "gs_check_status": [POINTER(GsWorkspace), c_void_p],
+    "gs_workspace_sort_bytes": [POINTER(GsWorkspace), POINTER(c_size_t), POINTER(c_size_t)],
     "gs_read_counters": [POINTER(GsWorkspace), POINTER(c_int64), c_void_p],
     "gs_copy_array": [POINTER(GsWorkspace), c_int32, c_void_p, c_size_t, c_void_p],
     "gs_sort_pairs": [POINTER(GsWorkspace), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,

@@ -763,6 +763,16 @@ int gs_graph_release(gs_workspace* ws) {
   return GS_OK;
 }
 
+int gs_workspace_sort_bytes(const gs_workspace* ws, size_t* depth_sort, size_t* pair_sort) {
+  if (!ws || !ws->base) return fail(GS_ERR_INVALID_ARG, "workspace is null or not initialised");
+  if (!depth_sort || !pair_sort) return fail(GS_ERR_INVALID_ARG, "null output");
+  auto span = [&](int first, int last_excl) { return (size_t)(ws->layout[last_excl] - ws->layout[first]); };
+  // the look-back words serve the depth and the pair passes alike: counted with the depth sort
+  *depth_sort = span(L_STATUS, L_STATUS + 1) + span(L_KEYS, L_VB + 1);
+  *pair_sort = span(L_PKA, L_PVB + 1);
+  return GS_OK;
+}
+
 int gs_check_status(gs_workspace* ws, gs_stream_t stream) {
   int rc = check_ws(ws);
   if (rc) return rc;

@@ -65,3 +65,32 @@ def test_budget_admission_on_gpu():
     stats = srv.run(_clone(reqs), realtime=False)
     assert stats["done"] == len(reqs)
     assert srv.peak_bytes <= budget and srv.peak_concurrency < 4
+
+
+def test_chunked_plan_under_a_tight_budget_matches_the_request_alone():
+    """A budget below every request's single-pass memory makes the server run
+    them in the memory-efficiency mode; with FP32 state the chunked render is
+    the single-pass render bit for bit, and the fine-tune gradients agree to
+    FP32 reassociation."""
+    scenes, reqs = _setup()
+    opts = gs.RasterOpts(state_format="fp32")
+    ex = CudaExecutor(scenes, 2, opts_fwd=opts, opts_bwd=opts, chunk_pairs=1 << 12)
+    plans = [ex.plans(r) for r in reqs]
+    assert all(len(p) == 2 for p in plans)
+    budget = max(p[1][0] for p in plans) + 1024       # fits every chunked plan, no single one
+    assert budget < min(p[0][0] for p in plans)
+    chunked = _clone(reqs)
+    stats = Server(ex, hbm_budget_bytes=budget, max_slots=2).run(chunked, realtime=False)
+    assert stats["done"] == len(reqs) and stats["plans"] == {"chunked": len(reqs)}
+    for r in reqs:
+        alone = _clone([r])
+        Server(CudaExecutor(scenes, 1, opts_fwd=opts, opts_bwd=opts), hbm_budget_bytes=8 << 30,
+               max_slots=1).run(alone, realtime=False)
+        a, c = alone[0].result, chunked[r.rid].result
+        assert alone[0].plan == "single"
+        assert torch.equal(a["image"], c["image"])
+        if r.backward:
+            assert abs(a["loss"] - c["loss"]) <= 1e-9 * abs(a["loss"])
+            for k in ("means", "scales", "quats", "opacities", "sh"):
+                x, y = a["grads"][k].double(), c["grads"][k].double()
+                assert (torch.linalg.norm(x - y) / torch.linalg.norm(x)).item() < 1e-5, k

@@ -104,3 +104,44 @@ def test_retry_requeues_at_the_front_and_keeps_arrival():
     assert ex.submitted.count(2) == 2
     # the retried request runs again before the ones that arrived after it
     assert ex.submitted.index(3) > len(ex.submitted) - 1 - ex.submitted[::-1].index(2)
+
+
+class PlanExecutor(FakeExecutor):
+    """Offers a fast plan and a smaller, slower one (the memory-efficiency mode)."""
+
+    def __init__(self, fast, small):
+        super().__init__({})
+        self.fast, self.small, self.ran = fast, small, {}
+
+    def plans(self, r):
+        return [(self.fast, "single"), (self.small, "chunked")]
+
+    def submit(self, r, slot, plan="single"):
+        self.ran[r.rid] = plan
+        return super().submit(r, slot)
+
+
+def test_admission_takes_the_smaller_plan_when_the_fast_one_does_not_fit():
+    # budget below the fast plan: every request runs chunked, none is rejected
+    ex = PlanExecutor(fast=120, small=30)
+    srv = Server(ex, hbm_budget_bytes=100, max_slots=4)
+    stats = srv.run(_reqs(12, gap=0.0))
+    assert stats["done"] == 12 and stats["rejected"] == 0
+    assert set(ex.ran.values()) == {"chunked"} and stats["plans"] == {"chunked": 12}
+    assert srv.peak_bytes <= 100 and srv.peak_concurrency == 3
+
+
+def test_admission_prefers_the_fast_plan_and_falls_back_under_pressure():
+    # room for one fast request; while it runs, the others take the small plan
+    ex = PlanExecutor(fast=60, small=20)
+    srv = Server(ex, hbm_budget_bytes=100, max_slots=4)
+    stats = srv.run(_reqs(8, gap=0.0))
+    assert stats["done"] == 8 and ex.ran[0] == "single"
+    assert "chunked" in set(ex.ran.values())
+    assert srv.peak_bytes <= 100
+
+
+def test_smallest_plan_over_budget_is_rejected():
+    ex = PlanExecutor(fast=500, small=200)
+    stats = Server(ex, hbm_budget_bytes=100, max_slots=2).run(_reqs(3))
+    assert stats["rejected"] == 3 and stats["done"] == 0
