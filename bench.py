@@ -41,6 +41,7 @@ KERNELS_PER_STAGE = {"project": 1, "sort": 5, "bin": None, "blend_fwd": 1, "loss
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FLOP_PER_FRAG_FWD = 20.0
 FLOP_PER_FRAG_BWD = 70.0
+REF_PIXELS = 64    # pixels traced per step of the reference (oracle) arm
 
 
 def parse():
@@ -52,7 +53,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_SPLATS, help="splat count (smaller for profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="main timed loop only (no fp16 run, e2e, CPU baseline, clocks)")
-    ap.add_argument("--cpu-pixels", type=int, default=48, help="pixels in the CPU-baseline sample")
+    ap.add_argument("--cpu-pixels", type=int, default=768, help="pixels in the CPU-baseline sample")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
@@ -299,6 +300,15 @@ def run_ours(args, rank, world, local_rank):
             stage_roof[s] = dict(bound="alu", achieved=round(ach, 3), unit="TFLOP/s",
                                  frac=round(ach / FP32_PEAK_TFLOPS, 4),
                                  frac_of_measured_fma=round(ach / fma_tflops, 4), ms=round(ms, 4))
+    # step bound: each stage at its own roofline (bytes / measured HBM peak, or
+    # flops / FP32 peak), summed over the stages; the step's fraction of it
+    bound_ms = {s: (amount / (hbm_peak * 1e9) if bound == "hbm"
+                    else amount / (FP32_PEAK_TFLOPS * 1e12)) * 1e3
+                for s, (bound, amount) in alg.items()}
+    step_bound = dict(ms=round(sum(bound_ms.values()), 4),
+                      stages_ms={s: round(v, 4) for s, v in bound_ms.items()},
+                      note="sum over stages of max(bytes / HBM peak, flops / FP32 peak) with each "
+                           "stage's algorithmic amount (one bound applies per stage)")
     dom = max(per_stage, key=per_stage.get)
     dr = stage_roof[dom]
     traffic = None
@@ -335,8 +345,9 @@ def run_ours(args, rank, world, local_rank):
                p99_ms=round(float(np.percentile(step_ms, 99)), 4),
                wall_ms_per_step=round(t_wall * 1e3 / args.steps, 4),
                gpu_launches=kernels_per_step * args.steps * world,
-               roofline=roofline)
+               roofline=roofline, step_bound=step_bound)
 
+    step_bound["frac_of_step"] = round(step_bound["ms"] / ms_per_view, 4)
     if not args.no_extras:
         # FP16 saved state, same work otherwise
         o16 = gs.RasterOpts(state_format="fp16", sh_degree=3, t_cull=1e-4)
@@ -682,17 +693,23 @@ def _source_hash(files):
 # ---------------------------------------------------------------------------
 def oracle_sample(scene_np, cam, target_np, n_pixels, seed):
     """One bounded sample of the view: full preprocessing (projection + depth
-    order of every splat) and forward + backward of n_pixels random pixels,
-    extrapolated to the whole image."""
+    order of every splat), the forward of n_pixels random pixels, the true
+    L1 gradient sign(C - target) there, and their backward; the tracing time
+    is extrapolated to the whole image (preprocessing counted once)."""
     import oracle
     rng = np.random.default_rng(seed)
     pix = rng.choice(cam.width * cam.height, size=n_pixels, replace=False).astype(np.int32)
-    g = np.sign(rng.uniform(-1, 1, size=(cam.height, cam.width, 3)))  # L1 loss gradient stand-in
+    opts = oracle.opts_array(t_cull=1e-4)
     t0 = time.perf_counter()
-    out = oracle.backward(scene_np, cam, g, oracle.opts_array(t_cull=1e-4), pixels=pix, timings=True)
+    fwd = oracle.render(scene_np, cam, opts, pixels=pix, timings=True)
+    g = np.zeros((cam.height * cam.width, 3))
+    g[pix] = np.sign(fwd["color"] - target_np.reshape(-1, 3)[pix].astype(np.float64))
+    out = oracle.backward(scene_np, cam, g, opts, pixels=pix, timings=True)
     wall = time.perf_counter() - t0
-    tm = out["timings"]
-    est_s = tm["preprocess_s"] + tm["trace_s"] * (cam.width * cam.height) / n_pixels
+    tf, tb = fwd["timings"], out["timings"]
+    trace = tf["trace_s"] + tb["trace_s"]
+    tm = dict(preprocess_s=tb["preprocess_s"], trace_s=trace)
+    est_s = tm["preprocess_s"] + trace * (cam.width * cam.height) / n_pixels
     return est_s, wall, tm
 
 
@@ -725,9 +742,10 @@ def cpu_baseline(args, scene_np, cam, target_np):
                 cpu_model=cpu_model(), kind="oracle",
                 tiny_scene_single_thread_ms=round(tiny_s * 1e3, 1),
                 sample=(f"FP64 oracle: projection + depth order of all {scene_np.n} splats "
-                        f"({tm['preprocess_s']:.2f}s) and fwd+bwd of {args.cpu_pixels} random pixels "
-                        f"({tm['trace_s']:.2f}s), trace time scaled by {cam.width * cam.height}/"
-                        f"{args.cpu_pixels} pixels; wall {wall:.1f}s"))
+                        f"({tm['preprocess_s']:.2f}s), then forward, true L1 gradient and backward "
+                        f"of {args.cpu_pixels} random pixels ({tm['trace_s']:.2f}s), trace time "
+                        f"scaled by {cam.width * cam.height}/{args.cpu_pixels} pixels; "
+                        f"wall {wall:.1f}s"))
 
 
 def run_reference(args, rank, world):
@@ -738,10 +756,12 @@ def run_reference(args, rank, world):
     scene_np, cam, target_np = syn.mipnerf_scene_3m(args.n)
     oracle.build()
     for w in range(args.warmup):
-        oracle_sample(scene_np, cam, target_np, 8, seed=w)
+        oracle_sample(scene_np, cam, target_np, 16, seed=w)
     ests, walls = [], []
+    # each step a bounded sample: REF_PIXELS pixels keep the whole --steps run
+    # within minutes (about a second per step on 16 cores)
     for k in range(args.steps):
-        est_s, wall, _ = oracle_sample(scene_np, cam, target_np, args.cpu_pixels, seed=1000 + k)
+        est_s, wall, _ = oracle_sample(scene_np, cam, target_np, REF_PIXELS, seed=1000 + k)
         ests.append(est_s)
         walls.append(wall)
     v = float(np.mean(ests)) * 1e3
@@ -753,8 +773,9 @@ def run_reference(args, rank, world):
                             t_cull=1e-4, loss="l1"),
                 cpu_baseline=dict(value=round(v, 1), unit="ms/view", cores=oracle.num_threads(),
                                   kind="oracle",
-                                  sample=f"per step: all-splat preprocessing + fwd+bwd of "
-                                         f"{args.cpu_pixels} random pixels, scaled to the full view"),
+                                  sample=f"per step: all-splat preprocessing + forward, true L1 "
+                                         f"gradient and backward of {REF_PIXELS} random "
+                                         f"pixels, trace time scaled to the full view"),
                 e2e=dict(value=round(v, 1), unit="ms/view", h2d_bytes_per_step=0,
                          d2h_bytes_per_step=0),
                 wall_s_per_step=round(float(np.mean(walls)), 2))

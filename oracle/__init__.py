@@ -123,8 +123,9 @@ def depth_order(scene, cam) -> np.ndarray:
     return order[:n]
 
 
-def render(scene, cam, opts=None, pixels=None):
-    """Forward render.  Returns dict(color [P,3] or [H,W,3], T, nfrag, last, ambig)."""
+def render(scene, cam, opts=None, pixels=None, timings: bool = False):
+    """Forward render.  Returns dict(color [P,3] or [H,W,3], T, nfrag, last, ambig)
+    (and timings: seconds of preprocessing and of tracing)."""
     opts = opts_array() if opts is None else opts
     keep, args = _scene_args(scene)
     camv = camera_array(cam)
@@ -139,13 +140,17 @@ def render(scene, cam, opts=None, pixels=None):
     nfrag = np.zeros(npix, dtype=np.int32)
     last = np.zeros(npix, dtype=np.int32)
     ambig = np.zeros(npix, dtype=np.int32)
+    tm = np.zeros(2)
     rc = _load().oracle_render(*args, _ptr(camv), _ptr(opts), _ptr(pix), ctypes.c_int(npix),
-                               _ptr(color), _ptr(T), _ptr(nfrag), _ptr(last), _ptr(ambig))
+                               _ptr(color), _ptr(T), _ptr(nfrag), _ptr(last), _ptr(ambig),
+                               _ptr(tm))
     assert rc == 0
     out = dict(color=color, T=T, nfrag=nfrag, last=last, ambig=ambig)
     if pixels is None:
         H, W = cam.height, cam.width
         out = {k: v.reshape((H, W, 3) if k == "color" else (H, W)) for k, v in out.items()}
+    if timings:
+        out["timings"] = dict(preprocess_s=float(tm[0]), trace_s=float(tm[1]))
     return out
 
 

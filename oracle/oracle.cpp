@@ -661,19 +661,23 @@ int oracle_depth_order(int N, const double* means, const double* scales, const d
 
 // Forward render of the listed pixels (linear index y*W+x), or of all pixels if
 // pixels == null.  color[npix][3], T[npix], nfrag[npix], last[npix], ambig[npix];
-// any output pointer may be null.
+// any output pointer may be null.  timings (if non-null) receives the seconds
+// spent in projection + depth order and in tracing.
 int oracle_render(int N, const double* means, const double* scales, const double* quats,
                   const double* opac, const double* sh, int deg, const double* camv,
                   const double* optv, const int32_t* pixels, int npix, double* color, double* Tout,
-                  int32_t* nfrag, int32_t* last, int32_t* ambig) {
+                  int32_t* nfrag, int32_t* last, int32_t* ambig, double* timings) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
   const Camera cam = read_camera(camv);
   const Opts op = read_opts(optv);
   Scene sc{N, means, scales, quats, opac, sh, deg};
   std::vector<Splat> sp;
   project_all(sc, cam, op.clamp01, sp);
   const std::vector<int> ord = depth_order(sp);
+  const auto t1 = clk::now();
   const int total = pixels ? npix : cam.W * cam.H;
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 1)
   for (int p = 0; p < total; ++p) {
     const int lin = pixels ? pixels[p] : p;
     PixelResult r;
@@ -689,6 +693,10 @@ int oracle_render(int N, const double* means, const double* scales, const double
     if (nfrag) nfrag[p] = r.nfrag;
     if (last) last[p] = r.last;
     if (ambig) ambig[p] = r.ambig;
+  }
+  if (timings) {
+    timings[0] = std::chrono::duration<double>(t1 - t0).count();
+    timings[1] = std::chrono::duration<double>(clk::now() - t1).count();
   }
   return 0;
 }
@@ -721,7 +729,7 @@ int oracle_backward(int N, const double* means, const double* scales, const doub
   {
     std::vector<Frag> fr;
     double* mine = acc.data() + static_cast<size_t>(thread_id()) * N * kG2;
-#pragma omp for schedule(dynamic, 8)
+#pragma omp for schedule(dynamic, 1)
     for (int q = 0; q < total; ++q) {
       const int p = pixels ? pixels[q] : q;
       PixelResult r;
