@@ -554,14 +554,13 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
         copied[k % 2].record(copy_st)
 
     def step_pipelined(k, last_k):
-        gs.zero_touched_gradients(ws, grads, st)   # rows of the previous view
         if k + 1 <= last_k:
             issue_copy(k + 1)
         st.wait_event(copied[k % 2])
+        # one graph: zero the previous view's gradient rows, the step, the loss to the host
         gs.render_batch([gs.Request(scene, ccam, opts, backward=True, loss_kind="l1",
-                                    target=tgt_buf[k % 2], outputs=gout)], ws, st, graph=True)
-        with torch.cuda.stream(st):
-            host_loss.copy_(loss, non_blocking=True)
+                                    target=tgt_buf[k % 2], outputs=gout, zero_touched=True,
+                                    loss_host=host_loss)], ws, st, graph=True)
 
     def timed_pipelined():
         st.wait_stream(stream)

@@ -167,6 +167,12 @@ typedef struct gs_request {
   float* d_quats;
   float* d_opacities;
   float* d_sh;
+  int32_t zero_touched;  /* forward+backward: first zero the gradient rows the workspace's last
+                            depth order touched (gs_zero_touched_gradients), so a training loop
+                            needs no separate reset of the previous view's rows */
+  int32_t pad0;
+  double* loss_host;     /* may be null: the loss is also copied to this pinned host double at
+                            the end of the request (inside the batch's CUDA graph) */
 } gs_request;
 
 /* Bytes of device workspace for scenes of up to n_cap splats and images of up

@@ -533,6 +533,8 @@ class Request:
     target: torch.Tensor | None = None
     dL_dimage: torch.Tensor | None = None
     outputs: dict = field(default_factory=dict)
+    zero_touched: bool = False                  # zero the previous view's gradient rows first
+    loss_host: torch.Tensor | None = None       # pinned float64 [1]: the loss copied there too
 
 
 def render_batch(requests, ws: Workspace, stream=None, graph: bool = False):
@@ -584,6 +586,12 @@ def render_batch(requests, ws: Workspace, stream=None, graph: bool = False):
             _check_grads(sc, g)
             c.d_means, c.d_scales, c.d_quats = _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"])
             c.d_opacities, c.d_sh = _ptr(g["opacities"]), _ptr(g["sh"])
+            c.zero_touched = int(bool(rq.zero_touched))
+            if rq.loss_host is not None:
+                if rq.loss_host.is_cuda or not rq.loss_host.is_pinned() or \
+                        rq.loss_host.dtype != torch.float64 or rq.loss_host.numel() < 1:
+                    raise ValueError("loss_host must be a pinned float64 host tensor")
+                c.loss_host = rq.loss_host.data_ptr()
     if graph:
         check(lib.gs_render_batch_graph(arr, len(requests), ws.ref, _stream(stream)),
               "gs_render_batch_graph")

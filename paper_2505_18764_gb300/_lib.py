@@ -64,7 +64,8 @@ class GsRequest(Structure):
                 ("state", c_void_p), ("last", c_void_p), ("n_contrib", c_void_p),
                 ("target", c_void_p), ("dL_dimage", c_void_p), ("loss", c_void_p),
                 ("d_means", c_void_p), ("d_scales", c_void_p), ("d_quats", c_void_p),
-                ("d_opacities", c_void_p), ("d_sh", c_void_p)]
+                ("d_opacities", c_void_p), ("d_sh", c_void_p), ("zero_touched", c_int32),
+                ("pad0", c_int32), ("loss_host", c_void_p)]
 
 
 _SIGS = {

@@ -671,8 +671,14 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
     const gs_request& q = reqs[i];
     if (q.opts.sh_degree != q.scene.sh_degree)
       return fail(GS_ERR_INVALID_ARG, "request %d: opts.sh_degree differs from the scene's", i);
-    int rc = gs_project(ws, q.scene.means, q.scene.scales, q.scene.quats, q.scene.opacities,
-                        q.scene.sh, q.scene.n, &q.camera, &q.opts, stream);
+    int rc = GS_OK;
+    // (a workspace that never projected has no previous view: nothing to zero)
+    if (q.mode == GS_MODE_FORWARD_BACKWARD && q.zero_touched && ws->n > 0)
+      rc = gs_zero_touched_gradients(ws, q.scene.n, q.d_means, q.d_scales, q.d_quats,
+                                     q.d_opacities, q.d_sh, stream);
+    if (!rc)
+      rc = gs_project(ws, q.scene.means, q.scene.scales, q.scene.quats, q.scene.opacities,
+                      q.scene.sh, q.scene.n, &q.camera, &q.opts, stream);
     if (!rc) rc = gs_sort(ws, stream);
     if (!rc) rc = gs_raster_forward(ws, &q.camera, &q.opts, q.image, q.state, q.last, q.n_contrib, stream);
     if (!rc && q.mode == GS_MODE_FORWARD_BACKWARD) {
@@ -686,6 +692,10 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
                                 q.scene.sh, q.scene.n, &q.camera, &q.opts, q.state, q.last,
                                 q.dL_dimage, q.d_means, q.d_scales, q.d_quats, q.d_opacities,
                                 q.d_sh, stream);
+      if (!rc && q.loss_host && q.loss_kind != GS_LOSS_NONE)
+        GS_CUDA(cudaMemcpyAsync(q.loss_host, q.loss, sizeof(double), cudaMemcpyDeviceToHost,
+                                reinterpret_cast<cudaStream_t>(stream)),
+                "loss copy to the host");
     } else if (!rc && q.mode != GS_MODE_FORWARD) {
       return fail(GS_ERR_INVALID_ARG, "request %d: bad mode %d", i, q.mode);
     }

@@ -466,6 +466,39 @@ def test_render_batch_matches_separate_calls():
         assert rel_l2(reqs[0].outputs["grads"][k].cpu().numpy(), grads[k].cpu().numpy()) < 1e-5
 
 
+def test_render_batch_zero_touched_and_host_loss_in_a_graph():
+    """A training loop's step as one graph: the request first zeroes the gradient
+    rows the previous view added to (zero_touched), then renders, back-propagates
+    and copies the loss to pinned host memory (loss_host).  Views after the first
+    give exactly the gradients of a fresh zeroed buffer, and the host loss is the
+    device loss."""
+    scene_np, cams = syn.precision_sweep_views(4)
+    opts = gs.RasterOpts()
+    scene = gs.SceneTensors.from_numpy(scene_np)
+    ws = gs.Workspace(scene.n, cams[0].width, cams[0].height, opts)
+    grads = gs.zero_grads(scene)
+    host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    for i, cam in enumerate(cams):
+        tgt = torch.rand((cam.height, cam.width, 3), device="cuda", generator=None)
+        rq = gs.Request(scene, cam, opts, backward=True, loss_kind="l2", target=tgt,
+                        outputs=dict(grads=grads), zero_touched=True, loss_host=host)
+        with torch.cuda.stream(st):
+            gs.render_batch([rq], ws, st, graph=True)
+        st.synchronize()
+        gs.check_status(ws, st)
+        fresh = gs.Request(scene, cam, opts, backward=True, loss_kind="l2", target=tgt)
+        ws2 = gs.Workspace(scene.n, cam.width, cam.height, opts)
+        gs.render_batch([fresh], ws2)
+        torch.cuda.synchronize()
+        assert host.item() == rq.outputs["loss"].item(), i
+        for k in GROUPS:
+            assert rel_l2(grads[k].cpu().numpy().astype(np.float64),
+                          fresh.outputs["grads"][k].cpu().numpy().astype(np.float64)) < 1e-5, (i, k)
+    ws.release_graph()
+
+
 def test_render_batch_graph_matches_direct():
     """The graph form of render_batch gives the direct form's results on its
     first call (run directly), its second (captured and instantiated), with a
