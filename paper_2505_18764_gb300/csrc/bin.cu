@@ -287,8 +287,19 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
       const uint32_t k = p - s_off[lo];
       const uint2 box = s_box[lo];
       const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
-      const uint32_t bx = (box.x & 0xFFFFu) + k % w;
-      const uint32_t by = (box.x >> 16) + min(k / w, h - 1);  // stays inside the box
+      // k / w and k % w through a float quotient corrected by one step (k and w
+      // below 2^22, so the estimate is off by at most one): no integer division
+      uint32_t qd = (uint32_t)__fdividef((float)k, (float)w);
+      int32_t rem = (int32_t)k - (int32_t)(qd * w);
+      if (rem < 0) {
+        --qd;
+        rem += (int32_t)w;
+      } else if (rem >= (int32_t)w) {
+        ++qd;
+        rem -= (int32_t)w;
+      }
+      const uint32_t bx = (box.x & 0xFFFFu) + (uint32_t)rem;
+      const uint32_t by = (box.x >> 16) + min(qd, h - 1);  // stays inside the box
       // blocks of the box that the ellipse misses get the key 0xFFFFFFFF, which
       // the first pass of the pair sort drops
       const SplatRec& R = rec_sorted[r0 + lo];
