@@ -244,24 +244,38 @@ __device__ __forceinline__ void fwd_item(FwdRing& R, const SplatRec* __restrict_
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], rx, ry,
                                                        rw, rh));
+    // two candidates at a time: their q and alpha do not depend on the pixel's
+    // state, so both are evaluated before the first blends (the second's hit
+    // is decided after the first may have T-culled the pixel)
     while (m) {
-      const int j = __ffs(m) - 1;
+      const int j1 = __ffs(m) - 1;
       m &= m - 1u;
-      const float4 a = R.a[slot][j];
-      const float4 b = R.b[slot][j];
-      float y1, y2a, y2b = 0.f, qa, qb = 0.f;
-      if (NPX == 2)
-        frag_q2(px, pya, pyb, a, b, y1, y2a, y2b, qa, qb);
-      else
-        qa = frag_q(px, pya, a, b, y1, y2a);
-      const bool ha = !pa.done && qa <= b.y;   // alpha >= 1/255
-      const bool hb = NPX == 2 && !pb.done && qb <= b.y;
-      if (!(ha || hb)) continue;
-      const float4 c = R.c[slot][j];
-      const uint32_t rank = R.rank[slot][j];
+      const bool two = m != 0u;
+      const int j2 = two ? __ffs(m) - 1 : j1;
+      if (two) m &= m - 1u;
+      const float4 a1 = R.a[slot][j1], b1 = R.b[slot][j1];
+      const float4 a2 = R.a[slot][j2], b2 = R.b[slot][j2];
+      float y1, y2a, y2b = 0.f, qa1, qb1 = 0.f, qa2, qb2 = 0.f;
+      if (NPX == 2) {
+        frag_q2(px, pya, pyb, a1, b1, y1, y2a, y2b, qa1, qb1);
+        frag_q2(px, pya, pyb, a2, b2, y1, y2a, y2b, qa2, qb2);
+      } else {
+        qa1 = frag_q(px, pya, a1, b1, y1, y2a);
+        qa2 = frag_q(px, pya, a2, b2, y1, y2a);
+      }
+      const float4 c1 = R.c[slot][j1], c2 = R.c[slot][j2];
+      const uint32_t rank1 = R.rank[slot][j1], rank2 = R.rank[slot][j2];
       float G, at;
-      if (ha) blend(pa, true, frag_alpha(c.w, qa, G, at), c, rank, t_cull);
-      if (NPX == 2 && hb) blend(pb, true, frag_alpha(c.w, qb, G, at), c, rank, t_cull);
+      const float alpha_a1 = frag_alpha(c1.w, qa1, G, at), alpha_a2 = frag_alpha(c2.w, qa2, G, at);
+      float alpha_b1 = 0.f, alpha_b2 = 0.f;
+      if (NPX == 2) {
+        alpha_b1 = frag_alpha(c1.w, qb1, G, at);
+        alpha_b2 = frag_alpha(c2.w, qb2, G, at);
+      }
+      if (!pa.done && qa1 <= b1.y) blend(pa, true, alpha_a1, c1, rank1, t_cull);
+      if (NPX == 2 && !pb.done && qb1 <= b1.y) blend(pb, true, alpha_b1, c1, rank1, t_cull);
+      if (two && !pa.done && qa2 <= b2.y) blend(pa, true, alpha_a2, c2, rank2, t_cull);
+      if (NPX == 2 && two && !pb.done && qb2 <= b2.y) blend(pb, true, alpha_b2, c2, rank2, t_cull);
     }
     __syncwarp();   // every lane is done with the slot before it is refilled
     ring_issue(R, slot, rec, ip, end, rk_next, lane);
