@@ -37,12 +37,13 @@ cudaError_t launch_bin_count(const uint32_t*, const SplatRec*, const uint2*, Spl
                              uint32_t, int, int, int, cudaStream_t);
 cudaError_t launch_bin_chunk(const uint32_t*, const uint2*, const SplatRec*, Header*, uint32_t*,
                              uint32_t, uint32_t, uint32_t, int, uint2*, uint32_t*, uint32_t*, int,
-                             int, int, int, cudaStream_t);
+                             int, int, int, cudaStream_t, uint32_t*, uint32_t*, int);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, int, cudaStream_t);
 cudaError_t launch_block_order(const uint2*, int, uint32_t, uint32_t*, Header*, cudaStream_t);
 cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint32_t*, uint32_t*,
                               const uint32_t*, const SplatRec*, int, int, int, int, float, int,
-                              float*, void*, uint32_t*, uint32_t*, int, int, cudaStream_t);
+                              float*, void*, uint32_t*, uint32_t*, int, uint32_t*, uint32_t*,
+                              uint32_t, int, cudaStream_t);
 cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, uint32_t*,
                               const Header*, uint32_t*, const uint32_t*, const SplatRec*, int, int,
                               int, int, float, int, const void*, const uint32_t*, const float*,
@@ -109,7 +110,9 @@ enum Slot {
   L_G2D,         // [n][12] backward accumulators by depth rank
   L_OFFSETS,     // [n] first pair index of each depth rank
   L_BOXES,       // [n] uint2 block box of each depth rank
-  L_CHUNK_STATE, // [width_cap * height_cap] float4 (C', T) between chunks (memory-efficiency mode)
+  L_CHUNK_STATE, // memory-efficiency mode: [width_cap * height_cap] float4 (g.C', T) between
+                 // chunks, then [2 blocks_cap] u32: the chunk after which each block's pixels
+                 // are all T-culled (0xFFFFFFFF: not yet), and this chunk's culled-pixel counts
   L_PKA, L_PVA, L_PKB, L_PVB,  // [pair_cap] pair ping-pong
   L_RANGES,      // [blocks_cap] uint2
   L_ORDER,       // [16 blocks_cap] u32 raster work items (warp footprints), longest lists first
@@ -148,7 +151,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, int c
   sz[L_OFFSETS] = n_cap * 4;
   sz[L_BOXES_ID] = n_cap * 8;
   sz[L_BOXES] = n_cap * 8;
-  sz[L_CHUNK_STATE] = chunked ? (size_t)w_cap * h_cap * 16 : 0;
+  sz[L_CHUNK_STATE] = chunked ? (size_t)w_cap * h_cap * 16 + blocks * 2 * 4 : 0;
   sz[L_PKA] = sz[L_PVA] = sz[L_PKB] = sz[L_PVB] = pair_cap * 4;
   sz[L_RANGES] = blocks * sizeof(uint2);
   sz[L_ORDER] = sz[L_ITEM_COST] = sz[L_BWD_ITEMS] = blocks * 16 * 4;
@@ -342,6 +345,18 @@ static int check_bound(gs_workspace* ws, const gs_camera* cam, const gs_raster_o
 
 namespace {
 
+// The memory-efficiency mode's per-block arrays (after the (g.C', T) carry in
+// L_CHUNK_STATE): which = 0 the chunk after which the block is done, 1 this
+// chunk's culled-pixel counts; null in the other modes.
+uint32_t* done_arrays(gs_workspace* ws, int which) {
+  if (!ws->chunked) return nullptr;
+  int gw, gh;
+  const size_t blocks = blocks_of(ws->width_cap, ws->height_cap, gw, gh);
+  return reinterpret_cast<uint32_t*>(at<char>(ws, L_CHUNK_STATE) +
+                                     (size_t)ws->width_cap * ws->height_cap * 16) +
+         (which ? blocks : 0);
+}
+
 // Binning, first pass: records into depth order, box pair counts, their scan.
 // skip_capacity: the whole view's pairs may exceed the capacity (the
 // memory-efficiency mode and depth slabs bin part of the view at a time).
@@ -364,7 +379,7 @@ int bin_count_stage(gs_workspace* ws, cudaStream_t st, int skip_capacity = -1) {
 // mode: 0 the whole view, 1 the memory-efficiency mode's chunk k of pair
 // budget B, 2 depth slab k of B (chunk_setup_kernel, bin.cu).
 int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
-                    uint32_t k, uint32_t B, cudaStream_t st, int mode = -1) {
+                    uint32_t k, uint32_t B, cudaStream_t st, int mode = -1, int reset_done = 0) {
   Header* hdr = at<Header>(ws, L_HDR);
   uint32_t* epoch = at<uint32_t>(ws, L_EPOCH);
   int gw, gh;
@@ -374,7 +389,8 @@ int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts
                            at<SplatRec>(ws, L_REC_SORTED), hdr, epoch, k, B, (uint32_t)ws->pair_cap,
                            mode >= 0 ? mode : ws->chunked, at<uint2>(ws, L_RANGES),
                            at<uint32_t>(ws, L_PKA),
-                           at<uint32_t>(ws, L_PVA), gw, gh, ws->pair_passes, grid_cap, st),
+                           at<uint32_t>(ws, L_PVA), gw, gh, ws->pair_passes, grid_cap, st,
+                           done_arrays(ws, 0), done_arrays(ws, 1), reset_done),
           "bin emit kernel");
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
   uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};
@@ -421,7 +437,7 @@ int count_chunks(gs_workspace* ws, const gs_camera* cam, cudaStream_t st, uint32
 
 int raster_fwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
                      float* image, void* state, uint32_t* last, uint32_t* n_contrib, int resume,
-                     cudaStream_t st) {
+                     cudaStream_t st, uint32_t chunk = 0) {
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
@@ -431,7 +447,7 @@ int raster_fwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
                             at<uint32_t>(ws, fin ? L_PVB : L_PVA),
                             at<SplatRec>(ws, L_REC_SORTED), cam->width, cam->height, gw, gh,
                             opts->t_cull, opts->state_format, image, state, last, n_contrib,
-                            resume, num_sms(), st),
+                            resume, done_arrays(ws, 0), done_arrays(ws, 1), chunk, num_sms(), st),
           "raster forward kernel");
   return GS_OK;
 }
@@ -507,8 +523,8 @@ int gs_raster_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
   if (rc) return rc;
   ws->n_chunks = (int32_t)n_chunks;
   for (uint32_t k = 0; k < n_chunks; ++k) {
-    rc = bin_chunk_stage(ws, cam, opts, k, B, st);
-    if (!rc) rc = raster_fwd_stage(ws, cam, opts, image, state, last, n_contrib, k > 0, st);
+    rc = bin_chunk_stage(ws, cam, opts, k, B, st, -1, k == 0);
+    if (!rc) rc = raster_fwd_stage(ws, cam, opts, image, state, last, n_contrib, k > 0, st, k);
     if (rc) return rc;
   }
   return GS_OK;

@@ -20,7 +20,9 @@
 // memory-efficiency mode the depth ranks are cut into chunks whose pairs fit
 // (chunk k holds the splats whose first pair index lies in [k B, (k + 1) B),
 // B = capacity - blocks, so no chunk exceeds the capacity) and each chunk is
-// emitted, sorted and rasterized in turn, front to back.
+// emitted, sorted and rasterized in turn, front to back; a block whose pixels
+// are all T-culled after chunk j gets no pairs in the chunks after j (they
+// would hold no fragment), which in dense views drops most of the pairs.
 #include "common.cuh"
 
 namespace gsr {
@@ -205,7 +207,9 @@ __global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __rest
                                                           uint32_t* __restrict__ epoch, uint32_t k,
                                                           uint32_t B, uint32_t pair_cap,
                                                           int mode, uint2* __restrict__ ranges,
-                                                          int nblocks) {
+                                                          int nblocks, uint32_t* __restrict__ block_done,
+                                                          uint32_t* __restrict__ done_px,
+                                                          int reset_done) {
   const uint32_t V = hdr->visible, total = hdr->pairs_wanted;
   if (threadIdx.x == 0) {
     uint32_t lo = 0, hi = min(total, pair_cap);
@@ -240,6 +244,10 @@ __global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __rest
   }
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&hdr->pair_hist[0][0])[i] = 0;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) ranges[i] = make_uint2(0, 0);
+  if (done_px)
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) done_px[i] = 0u;
+  if (block_done && reset_done)
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) block_done[i] = kNone;
 }
 
 // Pass 2: every CTA writes whole runs of kEmitChunk consecutive pairs of the
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
     const uint32_t* __restrict__ offsets, const uint2* __restrict__ boxes,
     const SplatRec* __restrict__ rec_sorted, Header* __restrict__ hdr,
     uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, int gw, int gh,
-    int pair_passes) {
+    int pair_passes, const uint32_t* __restrict__ block_done, uint32_t chunk) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   __shared__ uint2 s_box[kEmitChunk + 1];
   __shared__ uint32_t s_hist[4][256];
@@ -303,8 +311,12 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
       // blocks of the box that the ellipse misses get the key 0xFFFFFFFF, which
       // the first pass of the pair sort drops
       const SplatRec& R = rec_sorted[r0 + lo];
-      const bool hit = block_may_hit(R.a, R.b, (float)(bx * kBlock) + 0.5f, (float)(by * kBlock) + 0.5f);
-      const uint32_t key = hit ? by * (uint32_t)gw + bx : kNone;
+      // a block every pixel of which an earlier chunk left T-culled takes no
+      // more fragments: its pairs are dropped too
+      const uint32_t blk = by * (uint32_t)gw + bx;
+      const bool hit = block_may_hit(R.a, R.b, (float)(bx * kBlock) + 0.5f, (float)(by * kBlock) + 0.5f) &&
+                       !(block_done && block_done[blk] < chunk);
+      const uint32_t key = hit ? blk : kNone;
       pair_keys[p - pbase] = key;
       pair_vals[p - pbase] = r0 + lo;
       if (hit) {
@@ -448,16 +460,17 @@ cudaError_t launch_bin_chunk(const uint32_t* offsets, const uint2* boxes,
                              uint32_t B,
                              uint32_t pair_cap, int mode, uint2* ranges, uint32_t* pair_keys,
                              uint32_t* pair_vals, int gw, int gh, int pair_passes, int grid_cap,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint32_t* block_done, uint32_t* done_px,
+                             int reset_done) {
   chunk_setup_kernel<<<1, 256, 0, st>>>(offsets, hdr, epoch, k, B, pair_cap, mode, ranges,
-                                        gw * gh);
+                                        gw * gh, block_done, done_px, reset_done);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int runs = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
   if (runs > grid_cap) runs = grid_cap;
   if (runs < 1) runs = 1;
   bin_emit_kernel<<<runs, kBinThreads, 0, st>>>(offsets, boxes, rec_sorted, hdr, pair_keys,
-                                                pair_vals, gw, gh, pair_passes);
+                                                pair_vals, gw, gh, pair_passes, block_done, k);
   return cudaGetLastError();
 }
 

@@ -208,8 +208,10 @@ __device__ __forceinline__ void resume_fwd(PixelFwd& p, int x, int y, int W, int
   p.done = p.T < t_cull;
 }
 
+// Returns (warp-uniform) how many of the footprint's pixels in the image end
+// T-culled (the memory-efficiency mode's per-block count).
 template <int COLS>
-__device__ __forceinline__ void fwd_item(FwdRing& R, const SplatRec* __restrict__ rec,
+__device__ __forceinline__ uint32_t fwd_item(FwdRing& R, const SplatRec* __restrict__ rec,
                                          const uint32_t* __restrict__ pair_ranks, uint2 range,
                                          int x0, int y0, int lane, int W, int H, float t_cull,
                                          int fmt, float* image, void* state, uint32_t* last_out,
@@ -284,6 +286,8 @@ __device__ __forceinline__ void fwd_item(FwdRing& R, const SplatRec* __restrict_
   __syncwarp();
   if (wa) write_fwd(pa, x, ya, W, H, fmt, image, state, last_out, ncontrib);
   if (wb) write_fwd(pb, x, yb, W, H, fmt, image, state, last_out, ncontrib);
+  return (uint32_t)__popc(__ballot_sync(kFull, wa && pa.T < t_cull)) +
+         (uint32_t)__popc(__ballot_sync(kFull, wb && pb.T < t_cull));
 }
 
 __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
@@ -291,7 +295,8 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const Header* __restrict__ hdr, uint32_t* __restrict__ next, uint32_t* __restrict__ item_cost,
     const uint32_t* __restrict__ pair_ranks, const SplatRec* __restrict__ rec, int W, int H, int gw,
     float t_cull, int fmt, float* __restrict__ image, void* __restrict__ state,
-    uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib, int resume) {
+    uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncontrib, int resume,
+    uint32_t* __restrict__ block_done, uint32_t* __restrict__ done_px, uint32_t chunk) {
   __shared__ FwdRing rings[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   FwdRing& R = rings[warp];
@@ -301,16 +306,25 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const int cols = item_origin(items[idx], gw, block, x0, y0);
     const uint2 range = ranges[block];
     const long long t0 = clock64();
+    uint32_t culled;
     if (cols == 16)
-      fwd_item<16>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
-                   last_out, ncontrib, resume);
+      culled = fwd_item<16>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image,
+                            state, last_out, ncontrib, resume);
     else if (cols == 8)
-      fwd_item<8>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
-                  last_out, ncontrib, resume);
+      culled = fwd_item<8>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image,
+                           state, last_out, ncontrib, resume);
     else
-      fwd_item<4>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image, state,
-                  last_out, ncontrib, resume);
+      culled = fwd_item<4>(R, rec, pair_ranks, range, x0, y0, lane, W, H, t_cull, fmt, image,
+                           state, last_out, ncontrib, resume);
     if (lane == 0) item_cost[idx] = (uint32_t)min(clock64() - t0, (long long)0xFFFFFFFF);
+    // memory-efficiency mode: the item that completes the count of the block's
+    // T-culled pixels marks the block done after this chunk
+    if (block_done && lane == 0 && culled) {
+      const int bx = block % gw, by = block / gw;
+      const uint32_t valid = (uint32_t)(min(kBlock, W - bx * kBlock) * min(kBlock, H - by * kBlock));
+      // (the earliest such chunk stays: later chunks count the same pixels again)
+      if (atomicAdd(done_px + block, culled) + culled == valid) atomicMin(block_done + block, chunk);
+    }
   }
 }
 
@@ -1030,6 +1044,7 @@ cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const 
                               const SplatRec* rec,
                               int W, int H, int gw, int gh, float t_cull, int fmt, float* image,
                               void* state, uint32_t* last, uint32_t* ncontrib, int resume,
+                              uint32_t* block_done, uint32_t* done_px, uint32_t chunk,
                               int num_sms, cudaStream_t st) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
@@ -1042,7 +1057,7 @@ cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const 
   const int grid = per_sm * num_sms;
   raster_fwd_kernel<<<grid, kThreads, 0, st>>>(ranges, items, hdr, next, item_cost, pair_ranks, rec,
                                                W, H, gw, t_cull, fmt, image, state, last, ncontrib,
-                                               resume);
+                                               resume, block_done, done_px, chunk);
   return cudaGetLastError();
 }
 

@@ -779,6 +779,30 @@ def test_chunked_mode_matches_the_single_pass(which):
     _check_backward(scene_np, cam, oc, g)
 
 
+def test_chunked_mode_drops_the_pairs_of_t_culled_blocks():
+    """A dense view with T-culling in the memory-efficiency mode: once every
+    pixel of a block is T-culled, later chunks give the block no pairs (they
+    would hold no fragment), and the result is still the single pass bit for
+    bit (FP32 state) with the same gradients."""
+    scene_np = syn.cube_scene(30000, seed=89, sh_degree=1, log_scale_mean=-2.2)
+    cam = syn.look_at((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 40.0, 96, 64)
+    g = syn.uniform_image(cam.height, cam.width, seed=90, lo=-1.0, hi=1.0)
+    base = dict(sh_degree=1, t_cull=1e-2)
+    s1, ws1, out1, gr1 = run_forward_backward(scene_np, cam, gs.RasterOpts(**base), g)
+    c1 = gs.read_counters(ws1)
+    oc = gs.RasterOpts(chunked=True, pair_capacity=c1["pairs_wanted"] // 8 + 2 * 24, **base)
+    s2, ws2, out2, gr2 = run_forward_backward(scene_np, cam, oc, g)
+    c2 = gs.read_counters(ws2)   # the last chunk's emitted and kept pairs
+    print(f"{ws2.c.n_chunks} chunks; kept pairs: single pass {c1['live_pairs'] / c1['pairs']:.3f}, "
+          f"last chunk {c2['live_pairs'] / max(c2['pairs'], 1):.3f}")
+    assert ws2.c.n_chunks >= 6
+    assert c2["live_pairs"] < 0.2 * c2["pairs"] < 0.2 * c1["pairs"]
+    for key in ("image", "state", "last", "n_contrib"):
+        assert torch.equal(out1[key], out2[key]), key
+    for k in GROUPS:
+        assert rel_l2(gr2[k], gr1[k]) < 1e-5, k
+
+
 def test_chunked_mode_reduced_precision_state():
     """fp16 state rounds (C, T) at every chunk boundary, like the paper's
     render-target round trips; still within the reduced-state bounds."""
