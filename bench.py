@@ -559,7 +559,7 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
         st.wait_event(copied[k % 2])
         # one graph: zero the previous view's gradient rows, the step, the loss to the host
         gs.render_batch([gs.Request(scene, ccam, opts, backward=True, loss_kind="l1",
-                                    target=tgt_buf[k % 2], outputs=gout, zero_touched=True,
+                                    target=tgt_buf[k % 2], outputs=gout, zero_touched=2,
                                     loss_host=host_loss)], ws, st, graph=True)
 
     def timed_pipelined():

@@ -533,7 +533,7 @@ class Request:
     target: torch.Tensor | None = None
     dL_dimage: torch.Tensor | None = None
     outputs: dict = field(default_factory=dict)
-    zero_touched: bool = False                  # zero the previous view's gradient rows first
+    zero_touched: int = 0   # 1: zero the previous view's gradient rows first; 2: grads = this view's alone
     loss_host: torch.Tensor | None = None       # pinned float64 [1]: the loss copied there too
 
 
@@ -586,7 +586,7 @@ def render_batch(requests, ws: Workspace, stream=None, graph: bool = False):
             _check_grads(sc, g)
             c.d_means, c.d_scales, c.d_quats = _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"])
             c.d_opacities, c.d_sh = _ptr(g["opacities"]), _ptr(g["sh"])
-            c.zero_touched = int(bool(rq.zero_touched))
+            c.zero_touched = int(rq.zero_touched)
             if rq.loss_host is not None:
                 if rq.loss_host.is_cuda or not rq.loss_host.is_pinned() or \
                         rq.loss_host.dtype != torch.float64 or rq.loss_host.numel() < 1:

@@ -19,7 +19,10 @@ cudaError_t launch_project_fwd(const float*, const float*, const float*, const f
 cudaError_t launch_project_bwd(const float*, const float*, const float*, const float*, const float*,
                                int, int, const gs_camera&, int, const uint32_t*, const float*,
                                const Header*, float*, float*, float*, float*, float*, int,
-                               cudaStream_t);
+                               cudaStream_t, int);
+cudaError_t launch_copy_word(const uint32_t*, uint32_t*, cudaStream_t);
+cudaError_t launch_zero_left(int, int, const uint32_t*, const uint32_t*, const uint32_t*, float*,
+                             float*, float*, float*, float*, int, cudaStream_t);
 cudaError_t launch_zero_touched(int, int, const uint32_t*, const Header*, float*, float*, float*,
                                 float*, float*, int, cudaStream_t);
 cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,
@@ -544,11 +547,16 @@ int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
                           reinterpret_cast<cudaStream_t>(stream));
 }
 
-int gs_project_backward(gs_workspace* ws, const float* means, const float* scales,
-                        const float* quats, const float* opacities, const float* sh, int32_t n,
-                        const gs_camera* cam, const gs_raster_opts* opts, float* d_means,
-                        float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
-                        gs_stream_t stream) {
+}  // extern "C"
+
+namespace {
+// gs_project_backward; store_grads: write the visible splats' rows (zeros where
+// they have no gradient) instead of adding to them.
+int project_backward_impl(gs_workspace* ws, const float* means, const float* scales,
+                          const float* quats, const float* opacities, const float* sh, int32_t n,
+                          const gs_camera* cam, const gs_raster_opts* opts, float* d_means,
+                          float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                          gs_stream_t stream, int store_grads) {
   int rc = check_bound(ws, cam, opts);
   if (rc) return rc;
   if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
@@ -558,9 +566,21 @@ int gs_project_backward(gs_workspace* ws, const float* means, const float* scale
   GS_CUDA(launch_project_bwd(means, scales, quats, opacities, sh, ws->n, ws->sh_degree, *cam,
                              ws->clamp01, at<uint32_t>(ws, L_VB), at<float>(ws, L_G2D),
                              at<Header>(ws, L_HDR), d_means, d_scales, d_quats, d_opacities, d_sh,
-                             num_sms(), reinterpret_cast<cudaStream_t>(stream)),
+                             num_sms(), reinterpret_cast<cudaStream_t>(stream), store_grads),
           "projection backward kernel");
   return GS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int gs_project_backward(gs_workspace* ws, const float* means, const float* scales,
+                        const float* quats, const float* opacities, const float* sh, int32_t n,
+                        const gs_camera* cam, const gs_raster_opts* opts, float* d_means,
+                        float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                        gs_stream_t stream) {
+  return project_backward_impl(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
+                               d_scales, d_quats, d_opacities, d_sh, stream, 0);
 }
 
 int gs_zero_touched_gradients(gs_workspace* ws, int32_t n, float* d_means, float* d_scales,
@@ -578,12 +598,15 @@ int gs_zero_touched_gradients(gs_workspace* ws, int32_t n, float* d_means, float
   return GS_OK;
 }
 
-int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales,
-                       const float* quats, const float* opacities, const float* sh, int32_t n,
-                       const gs_camera* cam, const gs_raster_opts* opts, const void* state,
-                       const uint32_t* last, const float* dL_dimage, float* d_means,
-                       float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
-                       gs_stream_t stream) {
+}  // extern "C"
+
+namespace {
+int raster_backward_impl(gs_workspace* ws, const float* means, const float* scales,
+                         const float* quats, const float* opacities, const float* sh, int32_t n,
+                         const gs_camera* cam, const gs_raster_opts* opts, const void* state,
+                         const uint32_t* last, const float* dL_dimage, float* d_means,
+                         float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                         gs_stream_t stream, int store_grads) {
   int rc = check_bound(ws, cam, opts);
   if (rc) return rc;
   if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
@@ -609,8 +632,21 @@ int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales
     }
   }
   if (rc) return rc;
-  return gs_project_backward(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
-                             d_scales, d_quats, d_opacities, d_sh, stream);
+  return project_backward_impl(ws, means, scales, quats, opacities, sh, n, cam, opts, d_means,
+                               d_scales, d_quats, d_opacities, d_sh, stream, store_grads);
+}
+}  // namespace
+
+extern "C" {
+
+int gs_raster_backward(gs_workspace* ws, const float* means, const float* scales,
+                       const float* quats, const float* opacities, const float* sh, int32_t n,
+                       const gs_camera* cam, const gs_raster_opts* opts, const void* state,
+                       const uint32_t* last, const float* dL_dimage, float* d_means,
+                       float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
+                       gs_stream_t stream) {
+  return raster_backward_impl(ws, means, scales, quats, opacities, sh, n, cam, opts, state, last,
+                              dL_dimage, d_means, d_scales, d_quats, d_opacities, d_sh, stream, 0);
 }
 
 int gs_raster_forward_slab(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
@@ -688,13 +724,29 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
     if (q.opts.sh_degree != q.scene.sh_degree)
       return fail(GS_ERR_INVALID_ARG, "request %d: opts.sh_degree differs from the scene's", i);
     int rc = GS_OK;
+    if (q.zero_touched < 0 || q.zero_touched > 2)
+      return fail(GS_ERR_INVALID_ARG, "request %d: bad zero_touched %d", i, q.zero_touched);
+    const bool fb = q.mode == GS_MODE_FORWARD_BACKWARD;
+    const bool store = fb && q.zero_touched == 2;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // (a workspace that never projected has no previous view: nothing to zero)
-    if (q.mode == GS_MODE_FORWARD_BACKWARD && q.zero_touched && ws->n > 0)
+    if (fb && q.zero_touched == 1 && ws->n > 0)
       rc = gs_zero_touched_gradients(ws, q.scene.n, q.d_means, q.d_scales, q.d_quats,
                                      q.d_opacities, q.d_sh, stream);
+    if (!rc && store) {   // the previous view's visible count survives the projection here
+      if (q.scene.n > 0 && (!q.d_means || !q.d_scales || !q.d_quats || !q.d_opacities || !q.d_sh))
+        return fail(GS_ERR_INVALID_ARG, "request %d: null gradient pointer", i);
+      GS_CUDA(launch_copy_word(&at<Header>(ws, L_HDR)->visible, at<uint32_t>(ws, L_EPOCH) + 1, st),
+              "visible count copy");
+    }
     if (!rc)
       rc = gs_project(ws, q.scene.means, q.scene.scales, q.scene.quats, q.scene.opacities,
                       q.scene.sh, q.scene.n, &q.camera, &q.opts, stream);
+    if (!rc && store)   // rows of the splats that left the view (before the sort replaces the order)
+      GS_CUDA(launch_zero_left(q.scene.n, q.scene.sh_degree, at<uint32_t>(ws, L_VB),
+                               at<uint32_t>(ws, L_EPOCH) + 1, at<uint32_t>(ws, L_KEYS), q.d_means,
+                               q.d_scales, q.d_quats, q.d_opacities, q.d_sh, num_sms(), st),
+              "gradient zeroing kernel");
     if (!rc) rc = gs_sort(ws, stream);
     if (!rc) rc = gs_raster_forward(ws, &q.camera, &q.opts, q.image, q.state, q.last, q.n_contrib, stream);
     if (!rc && q.mode == GS_MODE_FORWARD_BACKWARD) {
@@ -704,10 +756,10 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
         rc = gs_loss(q.image, q.target, nv, q.loss_kind, q.dL_dimage, q.loss, stream);
       }
       if (!rc)
-        rc = gs_raster_backward(ws, q.scene.means, q.scene.scales, q.scene.quats, q.scene.opacities,
-                                q.scene.sh, q.scene.n, &q.camera, &q.opts, q.state, q.last,
-                                q.dL_dimage, q.d_means, q.d_scales, q.d_quats, q.d_opacities,
-                                q.d_sh, stream);
+        rc = raster_backward_impl(ws, q.scene.means, q.scene.scales, q.scene.quats,
+                                  q.scene.opacities, q.scene.sh, q.scene.n, &q.camera, &q.opts,
+                                  q.state, q.last, q.dL_dimage, q.d_means, q.d_scales, q.d_quats,
+                                  q.d_opacities, q.d_sh, stream, store);
       if (!rc && q.loss_host && q.loss_kind != GS_LOSS_NONE)
         GS_CUDA(cudaMemcpyAsync(q.loss_host, q.loss, sizeof(double), cudaMemcpyDeviceToHost,
                                 reinterpret_cast<cudaStream_t>(stream)),

@@ -399,8 +399,8 @@ __device__ __forceinline__ void gather_rows(float* rows, int off, const float* _
   }
 }
 
-// dst[id_j * len + c] += rows[j * pitch + off + c], laid out as gather_rows.
-template <int LEN, int PITCH>
+// dst[id_j * len + c] += rows[j * pitch + off + c] (STORE: =), laid out as gather_rows.
+template <int LEN, int PITCH, bool STORE = false>
 __device__ __forceinline__ void scatter_add_rows(const float* rows, int off,
                                                  float* __restrict__ dst, uint32_t id, int count,
                                                  int lane) {
@@ -408,7 +408,12 @@ __device__ __forceinline__ void scatter_add_rows(const float* rows, int off,
   for (int t = 0; t < LEN; ++t) {
     const int i = t * 32 + lane, j = i / LEN, c = i % LEN;
     const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
-    if (j < count) dst[(size_t)idj * LEN + c] += rows[j * PITCH + off + c];
+    if (j < count) {
+      if (STORE)
+        dst[(size_t)idj * LEN + c] = rows[j * PITCH + off + c];
+      else
+        dst[(size_t)idj * LEN + c] += rows[j * PITCH + off + c];
+    }
   }
 }
 
@@ -426,7 +431,7 @@ __device__ __forceinline__ void gather_rows4(float* rows, int off, const float* 
   }
 }
 
-template <int LEN4, int PITCH>
+template <int LEN4, int PITCH, bool STORE = false>
 __device__ __forceinline__ void scatter_add_rows4(const float* rows, int off,
                                                   float* __restrict__ dst, uint32_t id, int count,
                                                   int lane) {
@@ -437,9 +442,13 @@ __device__ __forceinline__ void scatter_add_rows4(const float* rows, int off,
     const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
     if (j < count) {
       const float4 g = *reinterpret_cast<const float4*>(rows + j * PITCH + off + 4 * c);
-      float4 v = d4[(size_t)idj * LEN4 + c];
-      v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w;
-      d4[(size_t)idj * LEN4 + c] = v;
+      if (STORE) {
+        d4[(size_t)idj * LEN4 + c] = g;
+      } else {
+        float4 v = d4[(size_t)idj * LEN4 + c];
+        v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w;
+        d4[(size_t)idj * LEN4 + c] = v;
+      }
     }
   }
 }
@@ -569,8 +578,9 @@ __device__ __forceinline__ float4 project_bwd_splat(float* row, const float4 qua
                      (gq[2] - y * qd) * ps.rq, (gq[3] - z * qd) * ps.rq);
 }
 
-// One batch of `count` (<= 32) queued ranks, lane j holding rank r.
-template <int DEG>
+// One batch of `count` (<= 32) queued ranks, lane j holding rank r.  STORE:
+// the rows are written instead of added to.
+template <int DEG, bool STORE>
 __device__ __forceinline__ void project_bwd_batch(
     float* rows, uint32_t r, int count, int lane, const float* __restrict__ means,
     const float* __restrict__ scales, const float4* __restrict__ quats,
@@ -599,33 +609,54 @@ __device__ __forceinline__ void project_bwd_batch(
   __syncwarp();
   if (mine) {
     const float4 gq = project_bwd_splat<DEG>(rows + lane * P, quat, ga, gb, cam, clamp01);
-    if (dq_vec) {
-      float4* dq = reinterpret_cast<float4*>(d_quats) + id;
-      float4 q4 = *dq;
-      q4.x += gq.x; q4.y += gq.y; q4.z += gq.z; q4.w += gq.w;
-      *dq = q4;
+    if (STORE) {
+      if (dq_vec) {
+        reinterpret_cast<float4*>(d_quats)[id] = gq;
+      } else {
+        d_quats[4 * id + 0] = gq.x;
+        d_quats[4 * id + 1] = gq.y;
+        d_quats[4 * id + 2] = gq.z;
+        d_quats[4 * id + 3] = gq.w;
+      }
+      d_opac[id] = gop;
     } else {
-      d_quats[4 * id + 0] += gq.x;
-      d_quats[4 * id + 1] += gq.y;
-      d_quats[4 * id + 2] += gq.z;
-      d_quats[4 * id + 3] += gq.w;
+      if (dq_vec) {
+        float4* dq = reinterpret_cast<float4*>(d_quats) + id;
+        float4 q4 = *dq;
+        q4.x += gq.x; q4.y += gq.y; q4.z += gq.z; q4.w += gq.w;
+        *dq = q4;
+      } else {
+        d_quats[4 * id + 0] += gq.x;
+        d_quats[4 * id + 1] += gq.y;
+        d_quats[4 * id + 2] += gq.z;
+        d_quats[4 * id + 3] += gq.w;
+      }
+      d_opac[id] += gop;
     }
-    d_opac[id] += gop;
   }
   __syncwarp();
   // keep the gradient rows' loads below the chain rule: hoisted above it they
   // would hold a row's worth of registers through it
   asm volatile("" ::: "memory");
-  scatter_add_rows<3, P>(rows, 0, d_means, id, count, lane);
-  scatter_add_rows<3, P>(rows, 3, d_scales, id, count, lane);
+  scatter_add_rows<3, P, STORE>(rows, 0, d_means, id, count, lane);
+  scatter_add_rows<3, P, STORE>(rows, 3, d_scales, id, count, lane);
   if (Row::kVec && sh_vec)
-    scatter_add_rows4<Row::kSh / 4, P>(rows, Row::kShOff, d_sh, id, count, lane);
+    scatter_add_rows4<Row::kSh / 4, P, STORE>(rows, Row::kShOff, d_sh, id, count, lane);
   else
-    scatter_add_rows<Row::kSh, P>(rows, Row::kShOff, d_sh, id, count, lane);
+    scatter_add_rows<Row::kSh, P, STORE>(rows, Row::kShOff, d_sh, id, count, lane);
   __syncwarp();   // the rows are reused by the next batch
 }
 
 template <int DEG>
+__device__ __forceinline__ void zero_splat_rows(uint32_t id, int count, int lane, int sh_vec,
+                                                int dq_vec, float* __restrict__ d_means,
+                                                float* __restrict__ d_scales,
+                                                float* __restrict__ d_quats,
+                                                float* __restrict__ d_opac, float* __restrict__ d_sh);
+
+// STORE (a request's gradient alone): every visible splat's rows are written,
+// the chain rule's for splats with a gradient and zeros for the others.
+template <int DEG, bool STORE>
 __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float4* __restrict__ quats, const float* __restrict__ sh, int sh_vec, int dq_vec,
@@ -653,20 +684,32 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
              gb.y != 0.f || gb.z != 0.f || gb.w != 0.f || g[12 * r + 8] != 0.f;
     }
     const unsigned m = __ballot_sync(0xffffffffu, live);
+    if (STORE) {   // rows of visible splats without a gradient: zeros
+      const unsigned z = __ballot_sync(0xffffffffu, r < V && !live);
+      if (z) {
+        const uint32_t zid = (z >> lane) & 1u ? sorted_ids[r] : 0u;
+        // compacted: lane j takes the id of the j-th lane to zero
+        const int cnt = __popc(z);
+        const int src = lane < cnt ? (int)__fns(z, 0u, lane + 1) : 0;
+        const uint32_t cid = __shfl_sync(0xffffffffu, zid, src);
+        zero_splat_rows<DEG>(cid, cnt, lane, sh_vec, dq_vec, d_means, d_scales, d_quats, d_opac,
+                             d_sh);
+      }
+    }
     if (live) queue[queued + __popc(m & lanemask_lt())] = r;
     queued += __popc(m);
     __syncwarp();
     if (queued >= 32) {
       queued -= 32;
-      project_bwd_batch<DEG>(rows, queue[queued + lane], 32, lane, means, scales, quats, sh,
-                             sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d, d_means, d_scales,
-                             d_quats, d_opac, d_sh);
+      project_bwd_batch<DEG, STORE>(rows, queue[queued + lane], 32, lane, means, scales, quats,
+                                    sh, sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d, d_means,
+                                    d_scales, d_quats, d_opac, d_sh);
     }
   }
   if (queued > 0)
-    project_bwd_batch<DEG>(rows, lane < queued ? queue[lane] : 0u, queued, lane, means, scales,
-                           quats, sh, sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d, d_means,
-                           d_scales, d_quats, d_opac, d_sh);
+    project_bwd_batch<DEG, STORE>(rows, lane < queued ? queue[lane] : 0u, queued, lane, means,
+                                  scales, quats, sh, sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d,
+                                  d_means, d_scales, d_quats, d_opac, d_sh);
 }
 
 // Zeroing of the gradient rows of the last depth order's splats (the rows a
@@ -696,11 +739,30 @@ __device__ __forceinline__ void zero_rows4(float* __restrict__ dst, uint32_t id,
 }
 
 template <int DEG>
+__device__ __forceinline__ void zero_splat_rows(uint32_t id, int count, int lane, int sh_vec,
+                                                int dq_vec, float* __restrict__ d_means,
+                                                float* __restrict__ d_scales,
+                                                float* __restrict__ d_quats,
+                                                float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  constexpr int kSh = 3 * (DEG + 1) * (DEG + 1);
+  zero_rows<3>(d_means, id, count, lane);
+  zero_rows<3>(d_scales, id, count, lane);
+  zero_rows<1>(d_opac, id, count, lane);
+  if (dq_vec)
+    zero_rows4<1>(d_quats, id, count, lane);
+  else
+    zero_rows<4>(d_quats, id, count, lane);
+  if (kSh % 4 == 0 && sh_vec)
+    zero_rows4<(kSh % 4 == 0 ? kSh / 4 : 1)>(d_sh, id, count, lane);
+  else
+    zero_rows<kSh>(d_sh, id, count, lane);
+}
+
+template <int DEG>
 __global__ void __launch_bounds__(256) zero_touched_kernel(
     const uint32_t* __restrict__ sorted_ids, const Header* __restrict__ hdr, int sh_vec,
     int dq_vec, float* __restrict__ d_means, float* __restrict__ d_scales,
     float* __restrict__ d_quats, float* __restrict__ d_opac, float* __restrict__ d_sh) {
-  constexpr int kSh = 3 * (DEG + 1) * (DEG + 1);
   const uint32_t V = hdr->visible;
   const int lane = threadIdx.x & 31;
   // base is the same for the whole warp
@@ -708,19 +770,38 @@ __global__ void __launch_bounds__(256) zero_touched_kernel(
        base += gridDim.x * 256u) {
     const int count = (int)min(32u, V - base);
     const uint32_t id = lane < count ? sorted_ids[base + lane] : 0u;
-    zero_rows<3>(d_means, id, count, lane);
-    zero_rows<3>(d_scales, id, count, lane);
-    zero_rows<1>(d_opac, id, count, lane);
-    if (dq_vec)
-      zero_rows4<1>(d_quats, id, count, lane);
-    else
-      zero_rows<4>(d_quats, id, count, lane);
-    if (kSh % 4 == 0 && sh_vec)
-      zero_rows4<(kSh % 4 == 0 ? kSh / 4 : 1)>(d_sh, id, count, lane);
-    else
-      zero_rows<kSh>(d_sh, id, count, lane);
+    zero_splat_rows<DEG>(id, count, lane, sh_vec, dq_vec, d_means, d_scales, d_quats, d_opac,
+                         d_sh);
   }
 }
+
+// Rows of the splats the previous depth order held (prev_sorted_ids, prev_V of
+// them) that the current projection culled (keys 0xFFFFFFFF): the splats that
+// left the view.  With the current view's rows written by a store-mode
+// backward, the arrays then hold the current view's gradient alone.
+template <int DEG>
+__global__ void __launch_bounds__(256) zero_left_kernel(
+    const uint32_t* __restrict__ prev_sorted_ids, const uint32_t* __restrict__ prev_V,
+    const uint32_t* __restrict__ keys, uint32_t n, int sh_vec, int dq_vec,
+    float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
+    float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  const uint32_t V = min(*prev_V, n);
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = blockIdx.x * 256u + (threadIdx.x & ~31u); base < V;
+       base += gridDim.x * 256u) {
+    const uint32_t r = base + lane;
+    uint32_t id = r < V ? prev_sorted_ids[r] : 0u;
+    const bool left = r < V && id < n && keys[id] == kNone;
+    const unsigned z = __ballot_sync(0xffffffffu, left);
+    if (!z) continue;
+    const int cnt = __popc(z);
+    const int src = lane < cnt ? (int)__fns(z, 0u, lane + 1) : 0;
+    id = __shfl_sync(0xffffffffu, id, src);
+    zero_splat_rows<DEG>(id, cnt, lane, sh_vec, dq_vec, d_means, d_scales, d_quats, d_opac, d_sh);
+  }
+}
+
+__global__ void copy_word_kernel(const uint32_t* src, uint32_t* dst) { *dst = *src; }
 
 }  // namespace gsr
 
@@ -770,7 +851,7 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
                                const gs_camera& cam, int clamp01, const uint32_t* sorted_ids,
                                const float* g2d, const Header* hdr, float* d_means,
                                float* d_scales, float* d_quats, float* d_opac, float* d_sh,
-                               int num_sms, cudaStream_t st) {
+                               int num_sms, cudaStream_t st, int store) {
   (void)opac;
   int blocks = (n_cap + kProjBwdThreads - 1) / kProjBwdThreads;
   if (blocks == 0) return cudaSuccess;
@@ -781,10 +862,14 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
   const float4* q4 = reinterpret_cast<const float4*>(quats);
   const float4* g4 = reinterpret_cast<const float4*>(g2d);
 #define GS_PROJECT_BWD(D)                                                                      \
-  project_bwd_kernel<D><<<blocks, kProjBwdThreads, 0, st>>>(means, scales, q4, sh, sh_vec,     \
-                                                            dq_vec, cd, clamp01, sorted_ids,   \
-                                                            g4, hdr, d_means, d_scales,        \
-                                                            d_quats, d_opac, d_sh)
+  if (store)                                                                                   \
+    project_bwd_kernel<D, true><<<blocks, kProjBwdThreads, 0, st>>>(                           \
+        means, scales, q4, sh, sh_vec, dq_vec, cd, clamp01, sorted_ids, g4, hdr, d_means,      \
+        d_scales, d_quats, d_opac, d_sh);                                                      \
+  else                                                                                         \
+    project_bwd_kernel<D, false><<<blocks, kProjBwdThreads, 0, st>>>(                          \
+        means, scales, q4, sh, sh_vec, dq_vec, cd, clamp01, sorted_ids, g4, hdr, d_means,      \
+        d_scales, d_quats, d_opac, d_sh)
   switch (deg) {
     case 0: GS_PROJECT_BWD(0); break;
     case 1: GS_PROJECT_BWD(1); break;
@@ -792,6 +877,34 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
     default: GS_PROJECT_BWD(3); break;
   }
 #undef GS_PROJECT_BWD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_word(const uint32_t* src, uint32_t* dst, cudaStream_t st) {
+  copy_word_kernel<<<1, 1, 0, st>>>(src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_left(int n, int deg, const uint32_t* prev_sorted_ids,
+                             const uint32_t* prev_V, const uint32_t* keys, float* d_means,
+                             float* d_scales, float* d_quats, float* d_opac, float* d_sh,
+                             int num_sms, cudaStream_t st) {
+  int blocks = (n + 255) / 256;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > num_sms * 8) blocks = num_sms * 8;
+  const int sh_vec = ((uintptr_t)d_sh & 15) == 0;
+  const int dq_vec = ((uintptr_t)d_quats & 15) == 0;
+#define GS_ZERO_LEFT(D)                                                                         \
+  zero_left_kernel<D><<<blocks, 256, 0, st>>>(prev_sorted_ids, prev_V, keys, (uint32_t)n,       \
+                                              sh_vec, dq_vec, d_means, d_scales, d_quats, d_opac, \
+                                              d_sh)
+  switch (deg) {
+    case 0: GS_ZERO_LEFT(0); break;
+    case 1: GS_ZERO_LEFT(1); break;
+    case 2: GS_ZERO_LEFT(2); break;
+    default: GS_ZERO_LEFT(3); break;
+  }
+#undef GS_ZERO_LEFT
   return cudaGetLastError();
 }
 

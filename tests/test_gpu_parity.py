@@ -466,13 +466,17 @@ def test_render_batch_matches_separate_calls():
         assert rel_l2(reqs[0].outputs["grads"][k].cpu().numpy(), grads[k].cpu().numpy()) < 1e-5
 
 
-def test_render_batch_zero_touched_and_host_loss_in_a_graph():
-    """A training loop's step as one graph: the request first zeroes the gradient
-    rows the previous view added to (zero_touched), then renders, back-propagates
-    and copies the loss to pinned host memory (loss_host).  Views after the first
-    give exactly the gradients of a fresh zeroed buffer, and the host loss is the
-    device loss."""
-    scene_np, cams = syn.precision_sweep_views(4)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_render_batch_zero_touched_and_host_loss_in_a_graph(mode):
+    """A training loop's step as one graph: the request resets the previous
+    view's gradient rows (zero_touched 1: zero them, then add; 2: write this
+    view's rows and zero the rows of splats that left the view), renders,
+    back-propagates and copies the loss to pinned host memory (loss_host).
+    Close-up views at several orbit angles see different subsets of the scene;
+    every view gives exactly the gradients of a fresh zeroed buffer (zero rows
+    outside the view), and the host loss is the device loss."""
+    scene_np, _ = syn.precision_sweep_views(1)
+    cams = [syn.orbit_camera(a, 2.2, 35.0, 96, 80) for a in (0.0, 1.3, 2.6, 0.2, 4.0)]
     opts = gs.RasterOpts()
     scene = gs.SceneTensors.from_numpy(scene_np)
     ws = gs.Workspace(scene.n, cams[0].width, cams[0].height, opts)
@@ -480,10 +484,11 @@ def test_render_batch_zero_touched_and_host_loss_in_a_graph():
     host = torch.zeros(1, dtype=torch.float64).pin_memory()
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
+    visible = []
     for i, cam in enumerate(cams):
         tgt = torch.rand((cam.height, cam.width, 3), device="cuda", generator=None)
         rq = gs.Request(scene, cam, opts, backward=True, loss_kind="l2", target=tgt,
-                        outputs=dict(grads=grads), zero_touched=True, loss_host=host)
+                        outputs=dict(grads=grads), zero_touched=mode, loss_host=host)
         with torch.cuda.stream(st):
             gs.render_batch([rq], ws, st, graph=True)
         st.synchronize()
@@ -492,10 +497,14 @@ def test_render_batch_zero_touched_and_host_loss_in_a_graph():
         ws2 = gs.Workspace(scene.n, cam.width, cam.height, opts)
         gs.render_batch([fresh], ws2)
         torch.cuda.synchronize()
+        visible.append(gs.read_counters(ws2)["visible"])
         assert host.item() == rq.outputs["loss"].item(), i
         for k in GROUPS:
-            assert rel_l2(grads[k].cpu().numpy().astype(np.float64),
-                          fresh.outputs["grads"][k].cpu().numpy().astype(np.float64)) < 1e-5, (i, k)
+            a = grads[k].cpu().numpy().astype(np.float64)
+            b = fresh.outputs["grads"][k].cpu().numpy().astype(np.float64)
+            assert rel_l2(a, b) < 1e-5, (i, k)
+            assert np.all(a[np.all(b.reshape(b.shape[0], -1) == 0, axis=1)] == 0), (i, k)
+    assert 0 < min(visible) < max(visible) < scene.n, visible   # the views see different subsets
     ws.release_graph()
 
 
