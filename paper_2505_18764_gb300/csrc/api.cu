@@ -37,10 +37,11 @@ cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cu
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
 cudaError_t launch_bin_count(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*,
                              Header*, unsigned long long*, const uint32_t*, uint32_t*, uint2*,
-                             uint32_t, int, int, int, cudaStream_t);
+                             uint32_t, int, int, int, cudaStream_t, uint32_t*, uint32_t);
 cudaError_t launch_bin_chunk(const uint32_t*, const uint2*, const SplatRec*, Header*, uint32_t*,
                              uint32_t, uint32_t, uint32_t, int, uint2*, uint32_t*, uint32_t*, int,
-                             int, int, int, cudaStream_t, uint32_t*, uint32_t*, int);
+                             int, int, int, cudaStream_t, uint32_t*, uint32_t*, int,
+                             const uint32_t*, uint32_t);
 cudaError_t launch_ranges(const uint32_t*, const Header*, uint2*, int, int, cudaStream_t);
 cudaError_t launch_block_order(const uint2*, int, uint32_t, uint32_t*, Header*, cudaStream_t);
 cudaError_t launch_raster_fwd(const uint2*, const uint32_t*, const Header*, uint32_t*, uint32_t*,
@@ -58,6 +59,7 @@ cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double
                         cudaStream_t);
 size_t sort_tiles(size_t n);
 size_t bin_tiles(size_t n);
+size_t emit_run_table(size_t pair_cap);
 
 namespace {
 
@@ -111,7 +113,8 @@ enum Slot {
   L_BOXES_ID,    // [n] uint2 16x16-block box of each splat, by splat id
   L_REC_SORTED,  // [n] records by depth rank
   L_G2D,         // [n][12] backward accumulators by depth rank
-  L_OFFSETS,     // [n] first pair index of each depth rank
+  L_OFFSETS,     // [n] first pair index of each depth rank, then the emission's run table:
+                 // [pair_cap / 2048 + 2] the rank holding pair m * 2048
   L_BOXES,       // [n] uint2 block box of each depth rank
   L_CHUNK_STATE, // memory-efficiency mode: [width_cap * height_cap] float4 (g.C', T) between
                  // chunks, then [2 blocks_cap] u32: the chunk after which each block's pixels
@@ -151,7 +154,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, int c
   sz[L_KEYS] = n_cap * 4;
   sz[L_KA] = sz[L_VA] = sz[L_KB] = sz[L_VB] = n_cap * 4;
   sz[L_REC] = sz[L_REC_SORTED] = sz[L_G2D] = n_cap * sizeof(SplatRec);
-  sz[L_OFFSETS] = n_cap * 4;
+  sz[L_OFFSETS] = (n_cap + emit_run_table(pair_cap)) * 4;
   sz[L_BOXES_ID] = n_cap * 8;
   sz[L_BOXES] = n_cap * 8;
   sz[L_CHUNK_STATE] = chunked ? (size_t)w_cap * h_cap * 16 + blocks * 2 * 4 : 0;
@@ -372,7 +375,9 @@ int bin_count_stage(gs_workspace* ws, cudaStream_t st, int skip_capacity = -1) {
                            at<float>(ws, L_G2D), hdr, at<unsigned long long>(ws, L_SCAN),
                            at<uint32_t>(ws, L_EPOCH), at<uint32_t>(ws, L_OFFSETS),
                            at<uint2>(ws, L_BOXES), (uint32_t)ws->pair_cap,
-                           skip_capacity >= 0 ? skip_capacity : ws->chunked, ws->n, grid_cap, st),
+                           skip_capacity >= 0 ? skip_capacity : ws->chunked, ws->n, grid_cap, st,
+                           at<uint32_t>(ws, L_OFFSETS) + ws->n_cap,
+                           (uint32_t)emit_run_table(ws->pair_cap)),
           "bin count kernel");
   return GS_OK;
 }
@@ -393,7 +398,9 @@ int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts
                            mode >= 0 ? mode : ws->chunked, at<uint2>(ws, L_RANGES),
                            at<uint32_t>(ws, L_PKA),
                            at<uint32_t>(ws, L_PVA), gw, gh, ws->pair_passes, grid_cap, st,
-                           done_arrays(ws, 0), done_arrays(ws, 1), reset_done),
+                           done_arrays(ws, 0), done_arrays(ws, 1), reset_done,
+                           at<uint32_t>(ws, L_OFFSETS) + ws->n_cap,
+                           (uint32_t)emit_run_table(ws->pair_cap)),
           "bin emit kernel");
   uint32_t* pk[2] = {at<uint32_t>(ws, L_PKA), at<uint32_t>(ws, L_PKB)};
   uint32_t* pv[2] = {at<uint32_t>(ws, L_PVA), at<uint32_t>(ws, L_PVB)};

@@ -34,6 +34,7 @@ constexpr unsigned long long kBinAgg = 1ull << 30;
 constexpr unsigned long long kBinPre = 2ull << 30;
 constexpr unsigned long long kBinCount = (1ull << 30) - 1;
 constexpr int kEmitChunk = 2048;  // pairs written per CTA step of the emission pass
+constexpr int kEmitPer = kEmitChunk / kBinThreads;   // steps of 32 pairs per warp
 constexpr int kChunkWhole = 0, kChunkBudget = 1, kChunkSlab = 2;   // chunk_setup_kernel modes
 
 // Pass 1: one tile of 1024 depth ranks per step of a persistent loop.
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
     const uint2* __restrict__ boxes_by_id, SplatRec* __restrict__ rec_sorted,
     float4* __restrict__ g2d, Header* __restrict__ hdr,
     unsigned long long* __restrict__ scan_status, const uint32_t* __restrict__ epoch,
-    uint32_t* __restrict__ offsets, uint2* __restrict__ boxes, uint32_t pair_cap, int chunked) {
+    uint32_t* __restrict__ offsets, uint2* __restrict__ boxes, uint32_t pair_cap, int chunked,
+    uint32_t* __restrict__ run_first, uint32_t run_cap) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_cnt[kBinTile];
   __shared__ uint32_t s_warp[kBinThreads / 32];
@@ -167,7 +169,13 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
 #pragma unroll
     for (int k = 0; k < kBinItems; ++k) {
       const uint32_t r = base + tid * kBinItems + k;
-      if (r < V) offsets[r] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
+      if (r < V) {
+        offsets[r] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
+        // run table: this rank holds pair m kEmitChunk for each such m in its range
+        for (unsigned long long m = (run + kEmitChunk - 1) / kEmitChunk;
+             m * kEmitChunk < run + c4[k] && m < run_cap; ++m)
+          run_first[m] = r;
+      }
       run += c4[k];
     }
     __syncthreads();
@@ -250,31 +258,100 @@ __global__ void __launch_bounds__(256) chunk_setup_kernel(const uint32_t* __rest
     for (int i = threadIdx.x; i < nblocks; i += blockDim.x) block_done[i] = kNone;
 }
 
+// The ellipse q <= lim of one splat against rows of 16x16 blocks.  With (X, Y)
+// the offset of a pixel centre from the splat's centre, q = (i11 X)^2 +
+// (i22 (Y - k X))^2; at a fixed Y, q <= lim holds for |X - s Y| <=
+// sqrt(alpha lim - (i11 i22 Y)^2) / alpha, alpha = i11^2 + (k i22)^2, s =
+// k i22^2 / alpha.  The boundary's largest X, sqrt(lim) / i11, lies at Y = k
+// times it and its smallest at the mirror point; X along the boundary is
+// concave in Y, so over a band of rows the extremes are taken at those two Y
+// clamped into the band.  A block of the row is reached iff its columns meet
+// [X_min, X_max]: the same set as the minimum of q over the block's rectangle
+// against lim (rect_may_hit), evaluated once per row instead of once per block.
+// lim carries rect_may_hit's margin and the range is widened by a further
+// 0.1% + 0.01 px, so rounding never drops a block with a fragment; non-finite
+// values keep every column.
+struct RowTest {
+  float ax, bz, ay, bw;                 // centre, float-float
+  float slope, ia, alim, d2, ys, ye;
+
+  __device__ __forceinline__ void init(const float4& a, const float4& b) {
+    ax = a.x;
+    bz = b.z;
+    ay = a.y;
+    bw = b.w;
+    const float i11 = a.z, k = a.w, i22 = b.x;
+    const float lim = b.y + 0.01f + 1e-3f * b.y;
+    const float ki = k * i22;
+    const float alpha = fmaf(i11, i11, ki * ki);
+    ia = __fdividef(1.0f, alpha);
+    slope = ki * i22 * ia;
+    alim = alpha * lim;
+    const float d = i11 * i22;
+    d2 = d * d;
+    ys = k * __fdividef(sqrtf(lim), i11);
+    ye = fmaf(__fdividef(sqrtf(alim), d), 1.001f, 0.01f);   // |Y| extent, widened
+  }
+  // Columns [c_lo, c_hi] of block row `by` that the ellipse may reach (empty
+  // when c_lo > c_hi).
+  __device__ __forceinline__ void row(int by, int& c_lo, int& c_hi) const {
+    const float Y0 = ((float)(by * kBlock) + 0.5f - ay) - bw;
+    const float Y1 = Y0 + (float)(kBlock - 1);
+    if (Y0 > ye || Y1 < -ye) {
+      c_lo = 1;
+      c_hi = 0;
+      return;
+    }
+    const float yh = fminf(fmaxf(ys, Y0), Y1), yl = fminf(fmaxf(-ys, Y0), Y1);
+    const float xh = fmaf(slope, yh, sqrtf(fmaxf(0.0f, alim - d2 * yh * yh)) * ia);
+    const float xl = fmaf(slope, yl, -sqrtf(fmaxf(0.0f, alim - d2 * yl * yl)) * ia);
+    const float m = fmaf(1e-3f, xh - xl, 0.01f);
+    // column c spans X in [X0, X0 + 15], X0 = (16 c + 0.5 - a.x) - b.z
+    const float cx = ax + bz;
+    const float lo = (xl - m + cx - 15.5f) * (1.0f / kBlock);
+    const float hi = (xh + m + cx - 0.5f) * (1.0f / kBlock);
+    c_lo = (int)ceilf(fmaxf(lo, -1.0f));     // NaN -> -1, every column kept
+    c_hi = (int)floorf(fminf(hi, 65536.0f));
+  }
+};
+
 // Pass 2: every CTA writes whole runs of kEmitChunk consecutive pairs of the
 // chunk, so the work is even however the pairs are spread over splats.
-__global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
+__global__ void __launch_bounds__(kBinThreads, 4) bin_emit_kernel(
     const uint32_t* __restrict__ offsets, const uint2* __restrict__ boxes,
     const SplatRec* __restrict__ rec_sorted, Header* __restrict__ hdr,
     uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, int gw, int gh,
-    int pair_passes, const uint32_t* __restrict__ block_done, uint32_t chunk) {
+    int pair_passes, const uint32_t* __restrict__ block_done, uint32_t chunk,
+    const uint32_t* __restrict__ run_first, uint32_t run_cap) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   __shared__ uint2 s_box[kEmitChunk + 1];
   __shared__ uint32_t s_hist[4][256];
+  __shared__ uint32_t s_unit[kBinThreads / 32][32 * kEmitPer];   // per warp: (rank << 21) | block row
+  __shared__ uint32_t s_iv[kBinThreads / 32][32 * kEmitPer];     // its columns: lo | (hi + 1) << 16
   __shared__ uint32_t s_r0, s_r1;
   const int tid = threadIdx.x;
   for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
   const uint32_t P = hdr->pairs, V = hdr->visible, pbase = hdr->pair_base;
   const uint32_t nruns = (P + kEmitChunk - 1) / kEmitChunk;
+  // run-table entries written by the binning's first pass
+  const uint32_t nb = (uint32_t)min((unsigned long long)run_cap,
+                                    ((unsigned long long)hdr->pairs_wanted + kEmitChunk - 1) / kEmitChunk);
   uint32_t live = 0;
   for (uint32_t c = blockIdx.x; c < nruns; c += gridDim.x) {
     const uint32_t p0 = pbase + c * kEmitChunk;         // global pair indices [p0, p1)
     const uint32_t p1 = pbase + min(P, (c + 1) * kEmitChunk);
     __syncthreads();
+    // the ranks of the run's first and last pairs: from the run table where
+    // it has them (the rank of pair m kEmitChunk; for the last pair, the rank
+    // holding the next table pair, an upper bound), else by a warp search
     if (tid < 32) {
-      const uint32_t r = warp_rank_of_pair(offsets, V, p0, tid);
+      const uint32_t m = p0 / kEmitChunk;
+      const uint32_t r = (p0 % kEmitChunk == 0 && m < nb) ? run_first[m]
+                                                          : warp_rank_of_pair(offsets, V, p0, tid);
       if (tid == 0) s_r0 = r;
     } else if (tid < 64) {
-      const uint32_t r = warp_rank_of_pair(offsets, V, p1 - 1, tid - 32);
+      const uint32_t m = (p1 - 1) / kEmitChunk + 1;
+      const uint32_t r = m < nb ? run_first[m] : warp_rank_of_pair(offsets, V, p1 - 1, tid - 32);
       if (tid == 32) s_r1 = r;
     }
     __syncthreads();
@@ -286,42 +363,91 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
       s_box[i] = boxes[r0 + i];
     }
     __syncthreads();
-    for (uint32_t p = p0 + tid; p < p1; p += kBinThreads) {
-      int lo = 0, hi = (int)nr;  // last i with s_off[i] <= p
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_off[mid] <= p) lo = mid; else hi = mid;
+    // warp w writes the pairs [p0 + 256 w, + 256) in kEmitPer steps of 32
+    // consecutive pairs.  First every pair finds its rank, row and column, and
+    // the first pair of each box row in the range registers the row as a unit;
+    // then each lane tests one unit against the splat's ellipse (RowTest), so
+    // a row costs one test however many blocks it has; then every pair reads
+    // its unit's columns.
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t wp0 = p0 + (uint32_t)warp * (32 * kEmitPer);
+    if (wp0 < p1) {
+      uint32_t unit_mask[kEmitPer], bxy[kEmitPer], lov[kEmitPer];
+      uint32_t nunits = 0;
+      int lo = 0;
+#pragma unroll
+      for (int st = 0; st < kEmitPer; ++st) {
+        const uint32_t p = wp0 + 32u * st + (uint32_t)lane;
+        const bool valid = p < p1;
+        const uint32_t pc = valid ? p : p1 - 1;
+        // last i with s_off[i] <= pc; 32 pairs on, the rank is at most 32 higher
+        int a = st == 0 ? 0 : lo, b = st == 0 ? (int)nr : min((int)nr, lo + 33);
+        while (b - a > 1) {
+          const int mid = (a + b) >> 1;
+          if (s_off[mid] <= pc) a = mid; else b = mid;
+        }
+        lo = a;
+        const uint2 box = s_box[lo];
+        const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
+        const uint32_t k = pc - s_off[lo];
+        // k / w and k % w through a float quotient corrected by one step (k and
+        // w below 2^22, so the estimate is off by at most one): no integer division
+        uint32_t qd = (uint32_t)__fdividef((float)k, (float)w);
+        int32_t rem = (int32_t)k - (int32_t)(qd * w);
+        if (rem < 0) {
+          --qd;
+          rem += (int32_t)w;
+        } else if (rem >= (int32_t)w) {
+          ++qd;
+          rem -= (int32_t)w;
+        }
+        const uint32_t row = min(qd, h - 1);   // stays inside the box
+        const uint32_t bx = (box.x & 0xFFFFu) + (uint32_t)rem, by = (box.x >> 16) + row;
+        bxy[st] = (by << 16) | bx;
+        lov[st] = valid ? (uint32_t)lo : kNone;
+        const bool lead = valid && (rem == 0 || (st == 0 && lane == 0));
+        const uint32_t m = __ballot_sync(0xffffffffu, lead);
+        unit_mask[st] = m;
+        if (lead) s_unit[warp][nunits + __popc(m & lanemask_lt())] = ((uint32_t)lo << 21) | by;
+        nunits += __popc(m);
       }
-      const uint32_t k = p - s_off[lo];
-      const uint2 box = s_box[lo];
-      const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
-      // k / w and k % w through a float quotient corrected by one step (k and w
-      // below 2^22, so the estimate is off by at most one): no integer division
-      uint32_t qd = (uint32_t)__fdividef((float)k, (float)w);
-      int32_t rem = (int32_t)k - (int32_t)(qd * w);
-      if (rem < 0) {
-        --qd;
-        rem += (int32_t)w;
-      } else if (rem >= (int32_t)w) {
-        ++qd;
-        rem -= (int32_t)w;
+      __syncwarp();
+      for (uint32_t u = (uint32_t)lane; u < nunits; u += 32) {
+        const uint32_t dsc = s_unit[warp][u];
+        const SplatRec& R = rec_sorted[r0 + (dsc >> 21)];
+        RowTest rt;
+        rt.init(R.a, R.b);
+        int c_lo, c_hi;
+        rt.row((int)(dsc & 0x1FFFFFu), c_lo, c_hi);
+        c_lo = min(max(c_lo, 0), 65535);     // block columns are below 65536
+        c_hi = min(max(c_hi, -1), 65534);
+        s_iv[warp][u] = (uint32_t)c_lo | ((uint32_t)(c_hi + 1) << 16);
       }
-      const uint32_t bx = (box.x & 0xFFFFu) + (uint32_t)rem;
-      const uint32_t by = (box.x >> 16) + min(qd, h - 1);  // stays inside the box
-      // blocks of the box that the ellipse misses get the key 0xFFFFFFFF, which
-      // the first pass of the pair sort drops
-      const SplatRec& R = rec_sorted[r0 + lo];
-      // a block every pixel of which an earlier chunk left T-culled takes no
-      // more fragments: its pairs are dropped too
-      const uint32_t blk = by * (uint32_t)gw + bx;
-      const bool hit = block_may_hit(R.a, R.b, (float)(bx * kBlock) + 0.5f, (float)(by * kBlock) + 0.5f) &&
-                       !(block_done && block_done[blk] < chunk);
-      const uint32_t key = hit ? blk : kNone;
-      pair_keys[p - pbase] = key;
-      pair_vals[p - pbase] = r0 + lo;
-      if (hit) {
-        ++live;
-        for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xFF], 1u);
+      __syncwarp();
+      uint32_t before = 0;
+#pragma unroll
+      for (int st = 0; st < kEmitPer; ++st) {
+        if (lov[st] != kNone) {
+          const uint32_t m = unit_mask[st];
+          const uint32_t u = before + __popc(m & lanemask_lt()) + ((m >> lane) & 1u) - 1u;
+          const uint32_t iv = s_iv[warp][u];
+          const uint32_t bx = bxy[st] & 0xFFFFu, by = bxy[st] >> 16;
+          const uint32_t blk = by * (uint32_t)gw + bx;
+          // blocks of the box that the ellipse misses get the key 0xFFFFFFFF,
+          // which the first pass of the pair sort drops; so do, in the memory-
+          // efficiency mode, blocks every pixel of which an earlier chunk left
+          // T-culled (they take no more fragments)
+          const bool hit = bx >= (iv & 0xFFFFu) && bx + 1u <= (iv >> 16) &&
+                           !(block_done && block_done[blk] < chunk);
+          const uint32_t dst = wp0 + 32u * st + (uint32_t)lane - pbase;
+          pair_keys[dst] = hit ? blk : kNone;
+          pair_vals[dst] = r0 + lov[st];
+          if (hit) {
+            ++live;
+            for (int q = 0; q < pair_passes; ++q) atomicAdd(&s_hist[q][(blk >> (8 * q)) & 0xFF], 1u);
+          }
+        }
+        before += __popc(unit_mask[st]);
       }
     }
   }
@@ -336,16 +462,35 @@ __global__ void __launch_bounds__(kBinThreads) bin_emit_kernel(
 }
 
 // Block ranges [start, end) in the live pairs sorted by block id.  ranges must
-// be zero beforehand (the chunk setup clears them).
+// be zero beforehand (the chunk setup clears them).  Each thread reads eight
+// consecutive keys as two 16-byte words (more bytes in flight than one key per
+// thread) plus the key on either side.
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys,
                                                      const Header* __restrict__ hdr,
                                                      uint2* __restrict__ ranges, uint32_t nblocks) {
   const uint32_t P = hdr->live_pairs;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-    const uint32_t k = keys[i];
-    if (k >= nblocks) continue;
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-    if (i + 1 == P || keys[i + 1] != k) ranges[k].y = i + 1;
+  const uint32_t n8 = (P + 7) / 8;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n8; g += gridDim.x * blockDim.x) {
+    const uint32_t i0 = 8 * g;
+    uint32_t k[8];
+    if (i0 + 8 <= P) {   // keys is 256-byte aligned
+      const uint4 u = reinterpret_cast<const uint4*>(keys)[2 * g];
+      const uint4 v = reinterpret_cast<const uint4*>(keys)[2 * g + 1];
+      k[0] = u.x; k[1] = u.y; k[2] = u.z; k[3] = u.w;
+      k[4] = v.x; k[5] = v.y; k[6] = v.z; k[7] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) k[j] = i0 + j < P ? keys[i0 + j] : kNone;
+    }
+    const uint32_t before = i0 > 0 ? keys[i0 - 1] : kNone;
+    const uint32_t after = i0 + 8 < P ? keys[i0 + 8] : kNone;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t kk = k[j];
+      if (kk >= nblocks) continue;   // also the slots past P
+      if ((j ? k[j - 1] : before) != kk) ranges[kk].x = i0 + j;
+      if ((j < 7 ? k[j + 1] : after) != kk) ranges[kk].y = i0 + j + 1;
+    }
   }
 }
 
@@ -445,14 +590,33 @@ cudaError_t launch_bin_count(const uint32_t* sorted_ids, const SplatRec* rec,
                              const uint2* boxes_by_id, SplatRec* rec_sorted, float* g2d,
                              Header* hdr, unsigned long long* scan_status, const uint32_t* epoch,
                              uint32_t* offsets, uint2* boxes, uint32_t pair_cap, int chunked,
-                             int n_cap, int grid_cap, cudaStream_t st) {
+                             int n_cap, int grid_cap, cudaStream_t st, uint32_t* run_first,
+                             uint32_t run_cap) {
   int tiles = (n_cap + kBinTile - 1) / kBinTile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > grid_cap) tiles = grid_cap;
   bin_count_kernel<<<tiles, kBinThreads, 0, st>>>(sorted_ids, rec, boxes_by_id, rec_sorted,
                                                   reinterpret_cast<float4*>(g2d), hdr, scan_status,
-                                                  epoch, offsets, boxes, pair_cap, chunked);
+                                                  epoch, offsets, boxes, pair_cap, chunked,
+                                                  run_first, run_cap);
   return cudaGetLastError();
+}
+
+// CTAs of the emission resident at once: its runs are dealt out by a static
+// grid stride, so a CTA that only starts when others finish would add a wave.
+int emit_resident_ctas() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 4;
+  if (cache[dev] == 0) {
+    int occ = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bin_emit_kernel, kBinThreads, 0) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    cache[dev] = occ * sms;
+  }
+  return cache[dev];
 }
 
 cudaError_t launch_bin_chunk(const uint32_t* offsets, const uint2* boxes,
@@ -461,16 +625,18 @@ cudaError_t launch_bin_chunk(const uint32_t* offsets, const uint2* boxes,
                              uint32_t pair_cap, int mode, uint2* ranges, uint32_t* pair_keys,
                              uint32_t* pair_vals, int gw, int gh, int pair_passes, int grid_cap,
                              cudaStream_t st, uint32_t* block_done, uint32_t* done_px,
-                             int reset_done) {
+                             int reset_done, const uint32_t* run_first, uint32_t run_cap) {
   chunk_setup_kernel<<<1, 256, 0, st>>>(offsets, hdr, epoch, k, B, pair_cap, mode, ranges,
                                         gw * gh, block_done, done_px, reset_done);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int runs = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
   if (runs > grid_cap) runs = grid_cap;
+  if (runs > emit_resident_ctas()) runs = emit_resident_ctas();
   if (runs < 1) runs = 1;
   bin_emit_kernel<<<runs, kBinThreads, 0, st>>>(offsets, boxes, rec_sorted, hdr, pair_keys,
-                                                pair_vals, gw, gh, pair_passes, block_done, k);
+                                                pair_vals, gw, gh, pair_passes, block_done, k,
+                                                run_first, run_cap);
   return cudaGetLastError();
 }
 
@@ -481,5 +647,6 @@ cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges
 }
 
 size_t bin_tiles(size_t n) { return (n + kBinTile - 1) / kBinTile; }
+size_t emit_run_table(size_t pair_cap) { return pair_cap / kEmitChunk + 2; }
 
 }  // namespace gsr

@@ -3,10 +3,11 @@
 // The paper sorts splats by depth with a custom Onesweep sort whose length is
 // read on the device (Sec. 4.1).  Each pass here: every CTA takes the next tile
 // id from an atomic counter (so all lower tiles belong to CTAs that already
-// run), ranks its 2048 keys stably with warp match/ballot and per-warp digit
-// counters, publishes its per-digit counts, looks back over lower tiles for
-// their per-digit prefix (decoupled look-back), reorders the tile by digit in
-// shared memory and writes it out.
+// run), counts its 2048 keys per digit and publishes the counts at once, ranks
+// the keys stably (warp match and per-warp digit counters) into their places
+// in shared memory, looks back over lower tiles for their per-digit prefix
+// (decoupled look-back; publishing before the ranking lets later tiles find
+// the counts sooner) and writes the tile out.
 //
 // Look-back status words are 64-bit: [63:32] tag (epoch * 16 + pass, so words
 // of earlier passes or views never match), [31:30] flag (1 = tile aggregate,
@@ -72,7 +73,6 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wcnt[kSortWarps][256];
   __shared__ uint32_t s_gbase[256];
-  __shared__ uint32_t s_toff[256];
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t s_warp[kSortWarps];
@@ -81,6 +81,9 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   const uint32_t n = n_dev ? *n_dev : n_static;
   const uint32_t ntiles = (uint32_t)(((uint64_t)n + kSortTile - 1) / kSortTile);
   const uint32_t tag = (*epoch) * 16u + pass_id;
+  // global digit bases: the exclusive scan of the pass histogram (thread d)
+  uint32_t hist_total = 0;
+  const uint32_t gexcl = block_excl_scan256(hist[tid], s_warp, hist_total);
   // persistent: take tiles in order until none is left; a CTA only ever waits
   // on lower tiles, which running CTAs took earlier, so the waits end
   for (;;) {
@@ -91,31 +94,29 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   if (tile >= ntiles) break;
   const uint64_t base = (uint64_t)tile * kSortTile;
 
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  uint32_t key[kSortItems], val[kSortItems];
   bool present[kSortItems];
+  // every load first, at clamped indices (n >= 1 here), so that all of them
+  // are in flight together; then the presence tests
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const uint64_t idx = base + (uint64_t)warp * (32 * kSortItems) + k * 32 + lane;
+    const uint64_t ci = idx < n ? idx : (uint64_t)(n - 1);
+    key[k] = __ldcs(keys_in + ci);
+    val[k] = vals_in ? __ldcs(vals_in + ci) : (uint32_t)idx;
+  }
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const uint64_t idx = base + (uint64_t)warp * (32 * kSortItems) + k * 32 + lane;
     present[k] = idx < n;
-    key[k] = present[k] ? keys_in[idx] : kNone;
+    if (!present[k]) key[k] = kNone;
     if (drop_sentinel && key[k] == kNone) present[k] = false;
-    val[k] = vals_in ? (present[k] ? vals_in[idx] : 0u) : (uint32_t)idx;
   }
-  // stable rank within the warp, item by item (warp-striped order = input order)
+  // per-warp digit counts (order-free), so that the tile's aggregate is
+  // published before the ranking: later tiles then find it sooner
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const uint32_t d = present[k] ? ((key[k] >> shift) & mask) : 0x100u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t pre = 0;
-    if (lane == leader && present[k]) {
-      pre = s_wcnt[warp][d];
-      s_wcnt[warp][d] = pre + __popc(peers);
-    }
-    pre = __shfl_sync(0xffffffffu, pre, leader);
-    rank[k] = pre + __popc(peers & lanemask_lt());
-    __syncwarp();
-  }
+  for (int k = 0; k < kSortItems; ++k)
+    if (present[k]) atomicAdd(&s_wcnt[warp][(key[k] >> shift) & mask], 1u);
   __syncthreads();
   // per digit: warp-exclusive offsets and the tile total
   const uint32_t d = tid;
@@ -126,13 +127,37 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     s_wcnt[w][d] = tot;
     tot += c;
   }
-  // publish, then look back for the exclusive prefix over lower tiles
   unsigned long long* my = status + (uint64_t)tile * 256 + d;
+  st_relaxed64(my, make_status(tag, tile == 0 ? kFlagPre : kFlagAgg, tot));
+  // tile-local digit offsets; s_wcnt becomes each (warp, digit)'s first position
+  uint32_t tile_valid = 0;
+  const uint32_t toff = block_excl_scan256(tot, s_warp, tile_valid);
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) s_wcnt[w][d] += toff;
+  __syncthreads();
+  // stable rank within the warp, item by item (warp-striped order = input
+  // order), which is the item's position in the tile sorted by digit
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const uint32_t dk = present[k] ? ((key[k] >> shift) & mask) : 0x100u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dk);
+    const int leader = __ffs(peers) - 1;
+    uint32_t pre = 0;
+    if (lane == leader && present[k]) {
+      pre = s_wcnt[warp][dk];
+      s_wcnt[warp][dk] = pre + __popc(peers);
+    }
+    pre = __shfl_sync(0xffffffffu, pre, leader);
+    if (present[k]) {
+      const uint32_t pos = pre + __popc(peers & lanemask_lt());
+      s_keys[pos] = key[k];
+      s_vals[pos] = val[k];
+    }
+    __syncwarp();
+  }
+  // look back for the exclusive prefix over lower tiles
   uint32_t excl = 0;
-  if (tile == 0) {
-    st_relaxed64(my, make_status(tag, kFlagPre, tot));
-  } else {
-    st_relaxed64(my, make_status(tag, kFlagAgg, tot));
+  if (tile > 0) {
     // kLookWindow predecessors per round trip: their words are loaded together,
     // then consumed nearest first until a prefix or a word not yet published
     int64_t j = (int64_t)tile - 1;
@@ -164,22 +189,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     }
     st_relaxed64(my, make_status(tag, kFlagPre, (uint32_t)min((unsigned long long)excl + tot, kCount30)));
   }
-  // global digit bases (exclusive scan of hist) and tile-local digit offsets
-  uint32_t tile_valid = 0, hist_total = 0;
-  const uint32_t gexcl = block_excl_scan256(hist[d], s_warp, hist_total);
-  const uint32_t toff = block_excl_scan256(tot, s_warp, tile_valid);
-  s_toff[d] = toff;
   s_gbase[d] = gexcl + excl - toff;
-  __syncthreads();
-  // reorder the tile by digit in shared memory
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    if (!present[k]) continue;
-    const uint32_t dk = (key[k] >> shift) & mask;
-    const uint32_t pos = s_toff[dk] + s_wcnt[warp][dk] + rank[k];
-    s_keys[pos] = key[k];
-    s_vals[pos] = val[k];
-  }
   __syncthreads();
   for (uint32_t i = tid; i < tile_valid; i += kSortThreads) {
     const uint32_t kk = s_keys[i];
