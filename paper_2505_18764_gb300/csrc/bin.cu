@@ -374,19 +374,30 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_emit_kernel(
     if (wp0 < p1) {
       uint32_t unit_mask[kEmitPer], bxy[kEmitPer], lov[kEmitPer];
       uint32_t nunits = 0;
-      int lo = 0;
+      // rank of the warp's first pair (the same search on every lane)
+      int lo_base = 0;
+      {
+        int b = (int)nr;
+        while (b - lo_base > 1) {
+          const int mid = (lo_base + b) >> 1;
+          if (s_off[mid] <= wp0) lo_base = mid; else b = mid;
+        }
+      }
 #pragma unroll
       for (int st = 0; st < kEmitPer; ++st) {
-        const uint32_t p = wp0 + 32u * st + (uint32_t)lane;
+        const uint32_t q = wp0 + 32u * st;
+        const uint32_t p = q + (uint32_t)lane;
         const bool valid = p < p1;
+        // ranks starting inside this step: lane j looks at the j-th rank after
+        // lo_base (the rank of the pair before the step, or of its first pair
+        // in the first step); a rank starting at lane v counts for lanes >= v
+        const int j = lo_base + 1 + lane;
+        const uint32_t v = j < (int)nr ? s_off[j] - q : 32u;
+        const uint32_t starts = __reduce_or_sync(0xffffffffu,
+                                                 (v < 32u && (st > 0 || v > 0u)) ? 1u << v : 0u);
+        const int lo = lo_base + __popc(starts & (lanemask_lt() | (1u << lane)));
+        lo_base = __shfl_sync(0xffffffffu, lo, 31);
         const uint32_t pc = valid ? p : p1 - 1;
-        // last i with s_off[i] <= pc; 32 pairs on, the rank is at most 32 higher
-        int a = st == 0 ? 0 : lo, b = st == 0 ? (int)nr : min((int)nr, lo + 33);
-        while (b - a > 1) {
-          const int mid = (a + b) >> 1;
-          if (s_off[mid] <= pc) a = mid; else b = mid;
-        }
-        lo = a;
         const uint2 box = s_box[lo];
         const uint32_t w = max(box.y & 0xFFFFu, 1u), h = max(box.y >> 16, 1u);
         const uint32_t k = pc - s_off[lo];
