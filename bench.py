@@ -537,10 +537,12 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
 
     # The same step scheduled as a training loop would: step k+1's target is
     # copied up on a copy stream into the other of two buffers while step k
-    # computes, and the gradient rows the previous view's backward wrote (its
-    # visible splats) are zeroed instead of all n rows.  Every step still
-    # copies its own target up and reads its loss back inside the timed region.
-    # The step is one gs_render_batch_graph call (a CUDA graph) on its own stream.
+    # computes, and the gradient arrays hold this view's gradients alone without
+    # zeroing all n rows: the backward projection stores the visible splats'
+    # rows (zero_touched = 2) and the rows of splats that left the view are
+    # zeroed.  Every step still copies its own target up and reads its loss back
+    # (into pinned host memory, inside the graph) in the timed region.  The step
+    # is one gs_render_batch_graph call (a CUDA graph) on its own stream.
     st = torch.cuda.Stream(dev)
     copy_st = torch.cuda.Stream(dev)
     tgt_buf = [target, torch.empty_like(target)]
@@ -621,8 +623,9 @@ def run_e2e(args, gs, torch, scene, target, ccam, opts, dev, stream, image, stat
                 d2h_bytes_per_step=host_loss.numel() * host_loss.element_size(), steps=K,
                 inputs="target image up, loss down; scene parameters resident",
                 schedule="one gs_render_batch_graph call per step; next target copied up "
-                         "during the step; the gradient rows the previous view wrote are zeroed "
-                         "(gs_zero_touched_gradients)",
+                         "during the step; gradient rows stored for the visible splats and "
+                         "zeroed for those that left the view (zero_touched = 2); loss copied "
+                         "to pinned host memory in the graph",
                 serial=dict(value=v1, unit="ms/view",
                             schedule="copy up, zero all gradient rows, step, loss down, in one "
                                      "stream"),

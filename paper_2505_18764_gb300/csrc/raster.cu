@@ -364,7 +364,7 @@ __device__ __forceinline__ void batch_put(GradBatch& B, int s, int lane, uint32_
   B.col[(2 * s) * kColStride + row] = make_float4(v[0], v[1], v[2], v[3]);
   B.col[(2 * s + 1) * kColStride + row] = make_float4(v[4], v[5], v[6], v[7]);
   reinterpret_cast<float*>(&B.col[8 * kColStride + row])[s] = v[8];
-  if (lane == 0) B.rank[s] = rank;
+  B.rank[s] = rank;   // every lane stores the same value: no branch
 }
 
 // Sums of the batch's first n candidates, added to their accumulators.
@@ -710,8 +710,8 @@ __device__ __forceinline__ void bwd_item_pair(BwdRing& R, GradBatch& B,
       const float2 q = frag_q_pair(px, py, a, b, y1, y2);
       const bool ha = rank < pp.end_a && q.x <= b.y;
       const bool hb = rank < pp.end_b && q.y <= b.y;
-      if (!__any_sync(kFull, ha || hb)) continue;
       const float4 c = R.c[slot][j];
+      if (!__any_sync(kFull, ha || hb)) continue;
       float2 t[9];
       grad_pair(pp, ha, hb, q, y1, y2, a, b, c, t);
       if (MODE == GS_REDUCE_FRAGMENT) {

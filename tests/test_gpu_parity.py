@@ -100,8 +100,16 @@ def test_sort_pairs_matches_std_stable_sort(n, bits):
     np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), keys[order])
 
 
-def test_pair_lists_are_block_sorted_and_depth_ordered():
-    scene_np, cam, _ = syn.tiny_scene_1k()
+def _large_splat_view():
+    """400 splats of the tiny-scene distribution made ~7x larger (log-scale mean -1):
+    boxes of tens of blocks with many rows, where the emission's per-row test matters."""
+    scene_np = syn.cube_scene(400, seed=61, log_scale_mean=-1.0, log_scale_std=0.3)
+    return scene_np, syn.orbit_camera(0.4, 4.0, 60.0, 200, 168)
+
+
+@pytest.mark.parametrize("view", ["tiny", "large_splats"])
+def test_pair_lists_are_block_sorted_and_depth_ordered(view):
+    scene_np, cam = syn.tiny_scene_1k()[:2] if view == "tiny" else _large_splat_view()
     opts = gs.RasterOpts()
     scene, ws, _ = run_forward(scene_np, cam, opts)
     cnt = gs.read_counters(ws)
@@ -143,7 +151,7 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
     assert np.all((bx0 <= x0) & (bx0 + w - 1 >= x1) & (by0 <= y0) & (by0 + h - 1 >= y1))
     # and a live pair for every block holding a pixel centre with alpha >= 1/255
     # (outside a 1e-6 band of the cut), by brute force over each box
-    live = set((ranks * nblk + blocks).tolist())
+    live = np.sort(ranks * nblk + blocks)
     for r in range(V):
         xs = np.arange(max(0, int(np.floor(Pj[r, 1] - ex[r])) - 1), min(cam.width, int(np.ceil(Pj[r, 1] + ex[r])) + 2))
         ys = np.arange(max(0, int(np.floor(Pj[r, 2] - ey[r])) - 1), min(cam.height, int(np.ceil(Pj[r, 2] + ey[r])) + 2))
@@ -152,9 +160,11 @@ def test_pair_lists_are_block_sorted_and_depth_ordered():
         power = -0.5 * (Pj[r, 6] * dx * dx + 2 * Pj[r, 7] * dx * dy + Pj[r, 8] * dy * dy)
         cut = np.log(1.0 / (255.0 * o[r]))
         inside = power >= cut + 1e-6 * max(1.0, abs(cut))
-        for yy, xx in zip(*np.nonzero(inside)):
-            b = (int(ys[yy]) >> 4) * gw + (int(xs[xx]) >> 4)
-            assert r * nblk + b in live, (r, b)
+        yy, xx = np.nonzero(inside)
+        want = np.unique(r * nblk + (ys[yy] >> 4) * gw + (xs[xx] >> 4))
+        pos = np.searchsorted(live, want)
+        ok = (pos < live.size) & (live[np.minimum(pos, live.size - 1)] == want)
+        assert ok.all(), (r, want[~ok][:5] - r * nblk)
 
 
 # ---------------------------------------------------------------------------
