@@ -29,7 +29,7 @@ cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, ui
                                  const uint32_t*, uint32_t, uint32_t, uint32_t, int, uint32_t,
                                  const uint32_t*, unsigned long long*, uint32_t*, const uint32_t*,
                                  uint32_t, uint32_t*, int, int, cudaStream_t,
-                                 uint32_t spin_limit = kSpinLimit);
+                                 uint32_t spin_limit = kSpinLimit, int wide = 0);
 cudaError_t launch_set_word(uint32_t*, uint32_t, cudaStream_t);
 int noalloc_stalled_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int32_t,
                          uint32_t, cudaStream_t);
@@ -328,10 +328,13 @@ int gs_sort(gs_workspace* ws, gs_stream_t stream) {
     const uint32_t* vin = pass == 0 ? nullptr : bufs_v[(pass + 1) & 1];
     uint32_t* kout = bufs_k[pass & 1];
     uint32_t* vout = bufs_v[pass & 1];
+    // the first pass reads all n keys (wide tiles from 2M on); the others only
+    // the visible ones, usually far fewer (narrow tiles keep enough of them)
     GS_CUDA(launch_onesweep_pass(kin, vin, kout, vout, pass == 0 ? nullptr : &hdr->visible,
                                  (uint32_t)ws->n, (uint32_t)ws->n, (uint32_t)ws->n, 8 * pass, 0xFFu,
                                  hdr->depth_hist[pass], status, &hdr->tile_counter[pass], epoch,
-                                 (uint32_t)pass, &hdr->status, pass == 0, grid_cap, st),
+                                 (uint32_t)pass, &hdr->status, pass == 0, grid_cap, st, kSpinLimit,
+                                 pass == 0 && ws->n >= (1 << 21)),
             "depth sort pass");
   }
   return GS_OK;
@@ -412,7 +415,7 @@ int bin_chunk_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts
                                  (uint32_t)ws->pair_cap, (uint32_t)ws->pair_cap, 8 * q, 0xFFu,
                                  hdr->pair_hist[q], at<unsigned long long>(ws, L_STATUS),
                                  &hdr->tile_counter[4 + q], epoch, 4u + q, &hdr->status, q == 0,
-                                 grid_cap, st),
+                                 grid_cap, st, kSpinLimit, ws->pair_cap >= (1 << 22)),
             "pair sort pass");
   }
   const int fin = ws->pair_passes & 1;
@@ -947,7 +950,7 @@ int gs_sort_pairs(gs_workspace* ws, const uint32_t* keys_in, const uint32_t* val
     GS_CUDA(launch_onesweep_pass(kin, vin, kout, vout, nullptr, (uint32_t)n, (uint32_t)n, (uint32_t)n,
                                  8 * p, mask, hdr->depth_hist[p], at<unsigned long long>(ws, L_STATUS),
                                  &hdr->tile_counter[9 + p], epoch, 8u + p, &hdr->status, 0,
-                                 grid_cap, st),
+                                 grid_cap, st, kSpinLimit, n >= (1 << 22)),
             "sort pass");
   }
   return GS_OK;

@@ -63,6 +63,7 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_w
 // One pass.  Items with index >= n are absent; with drop_sentinel, items whose
 // key is 0xFFFFFFFF are absent too (culled splats).  vals_in == null means
 // value = index.  hist[256] holds the global digit counts of the present items.
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -70,16 +71,17 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     uint32_t mask, const uint32_t* __restrict__ hist, unsigned long long* __restrict__ status,
     uint32_t* __restrict__ tile_counter, const uint32_t* __restrict__ epoch, uint32_t pass_id,
     uint32_t* __restrict__ status_word, int drop_sentinel, uint32_t spin_limit) {
+  constexpr int TILE = kSortThreads * ITEMS;
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wcnt[kSortWarps][256];
   __shared__ uint32_t s_gbase[256];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_keys[TILE];
+  __shared__ uint32_t s_vals[TILE];
   __shared__ uint32_t s_warp[kSortWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t n = n_dev ? *n_dev : n_static;
-  const uint32_t ntiles = (uint32_t)(((uint64_t)n + kSortTile - 1) / kSortTile);
+  const uint32_t ntiles = (uint32_t)(((uint64_t)n + TILE - 1) / TILE);
   const uint32_t tag = (*epoch) * 16u + pass_id;
   // global digit bases: the exclusive scan of the pass histogram (thread d)
   uint32_t hist_total = 0;
@@ -92,22 +94,22 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   __syncthreads();
   const uint32_t tile = s_tile;
   if (tile >= ntiles) break;
-  const uint64_t base = (uint64_t)tile * kSortTile;
+  const uint64_t base = (uint64_t)tile * TILE;
 
-  uint32_t key[kSortItems], val[kSortItems];
-  bool present[kSortItems];
+  uint32_t key[ITEMS], val[ITEMS];
+  bool present[ITEMS];
   // every load first, at clamped indices (n >= 1 here), so that all of them
   // are in flight together; then the presence tests
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const uint64_t idx = base + (uint64_t)warp * (32 * kSortItems) + k * 32 + lane;
+  for (int k = 0; k < ITEMS; ++k) {
+    const uint64_t idx = base + (uint64_t)warp * (32 * ITEMS) + k * 32 + lane;
     const uint64_t ci = idx < n ? idx : (uint64_t)(n - 1);
     key[k] = __ldcs(keys_in + ci);
     val[k] = vals_in ? __ldcs(vals_in + ci) : (uint32_t)idx;
   }
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const uint64_t idx = base + (uint64_t)warp * (32 * kSortItems) + k * 32 + lane;
+  for (int k = 0; k < ITEMS; ++k) {
+    const uint64_t idx = base + (uint64_t)warp * (32 * ITEMS) + k * 32 + lane;
     present[k] = idx < n;
     if (!present[k]) key[k] = kNone;
     if (drop_sentinel && key[k] == kNone) present[k] = false;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   // per-warp digit counts (order-free), so that the tile's aggregate is
   // published before the ranking: later tiles then find it sooner
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k)
+  for (int k = 0; k < ITEMS; ++k)
     if (present[k]) atomicAdd(&s_wcnt[warp][(key[k] >> shift) & mask], 1u);
   __syncthreads();
   // per digit: warp-exclusive offsets and the tile total
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   // stable rank within the warp, item by item (warp-striped order = input
   // order), which is the item's position in the tile sorted by digit
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const uint32_t dk = present[k] ? ((key[k] >> shift) & mask) : 0x100u;
     const uint32_t peers = __match_any_sync(0xffffffffu, dk);
     const int leader = __ffs(peers) - 1;
@@ -229,13 +231,21 @@ cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_i
                                  uint32_t mask, const uint32_t* hist, unsigned long long* status,
                                  uint32_t* tile_counter, const uint32_t* epoch, uint32_t pass_id,
                                  uint32_t* status_word, int drop_sentinel, int grid_cap,
-                                 cudaStream_t st, uint32_t spin_limit) {
-  uint32_t tiles = (n_cap + kSortTile - 1) / kSortTile;
+                                 cudaStream_t st, uint32_t spin_limit, int wide) {
+  // wide: tiles of 4096 keys instead of 2048 (fewer look-back steps per key on
+  // long inputs; short inputs want more tiles)
+  const uint32_t tile = wide ? 2u * kSortTile : (uint32_t)kSortTile;
+  uint32_t tiles = (n_cap + tile - 1) / tile;
   if (tiles == 0) return cudaSuccess;
   if (tiles > (uint32_t)grid_cap) tiles = (uint32_t)grid_cap;
-  onesweep_pass_kernel<<<tiles, kSortThreads, 0, st>>>(
-      keys_in, vals_in, keys_out, vals_out, n_dev, n_static, out_cap, shift, mask, hist, status,
-      tile_counter, epoch, pass_id, status_word, drop_sentinel, spin_limit);
+  if (wide)
+    onesweep_pass_kernel<2 * kSortItems><<<tiles, kSortThreads, 0, st>>>(
+        keys_in, vals_in, keys_out, vals_out, n_dev, n_static, out_cap, shift, mask, hist, status,
+        tile_counter, epoch, pass_id, status_word, drop_sentinel, spin_limit);
+  else
+    onesweep_pass_kernel<kSortItems><<<tiles, kSortThreads, 0, st>>>(
+        keys_in, vals_in, keys_out, vals_out, n_dev, n_static, out_cap, shift, mask, hist, status,
+        tile_counter, epoch, pass_id, status_word, drop_sentinel, spin_limit);
   return cudaGetLastError();
 }
 
@@ -258,6 +268,6 @@ cudaError_t launch_set_word(uint32_t* p, uint32_t v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-size_t sort_tiles(size_t n) { return (n + kSortTile - 1) / kSortTile; }
+size_t sort_tiles(size_t n) { return (n + kSortTile - 1) / kSortTile; }   // the narrow tiles: an upper bound
 
 }  // namespace gsr

@@ -15,7 +15,7 @@ cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, ui
                                  const uint32_t*, uint32_t, uint32_t, uint32_t, int, uint32_t,
                                  const uint32_t*, unsigned long long*, uint32_t*, const uint32_t*,
                                  uint32_t, uint32_t*, int, int, cudaStream_t,
-                                 uint32_t spin_limit = kSpinLimit);
+                                 uint32_t spin_limit = kSpinLimit, int wide = 0);
 cudaError_t launch_set_word(uint32_t*, uint32_t, cudaStream_t);
 cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
