@@ -80,8 +80,9 @@ def test_depth_sort_is_stable_sort_of_gpu_keys():
     np.testing.assert_array_equal(ids, oracle.stable_sort_u32(keys)[:V])
 
 
+# (4M keys and more run 4096-key tiles; 4_194_305 leaves a one-key last tile)
 @pytest.mark.parametrize("n,bits", [(1, 8), (2047, 8), (2049, 13), (100003, 13), (250000, 32),
-                                    (70001, 24)])
+                                    (70001, 24), (4_194_305, 16), (5_000_000, 32)])
 def test_sort_pairs_matches_std_stable_sort(n, bits):
     rng = np.random.default_rng(n + bits)
     hi = 2 ** bits if bits < 32 else 2 ** 32
