@@ -33,8 +33,8 @@ constexpr int kBinTile = kBinThreads * kBinItems;  // 1024 ranks
 constexpr unsigned long long kBinAgg = 1ull << 30;
 constexpr unsigned long long kBinPre = 2ull << 30;
 constexpr unsigned long long kBinCount = (1ull << 30) - 1;
-constexpr int kEmitChunk = 2048;  // pairs written per CTA step of the emission pass
-constexpr int kEmitPer = kEmitChunk / kBinThreads;   // steps of 32 pairs per warp
+constexpr int kEmitPer = 8;                   // steps of 32 pairs in one warp task
+constexpr int kEmitTask = 32 * kEmitPer;       // pairs of one warp task of the emission (256)
 constexpr int kChunkWhole = 0, kChunkBudget = 1, kChunkSlab = 2;   // chunk_setup_kernel modes
 
 // Pass 1: one tile of 1024 depth ranks per step of a persistent loop.
@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
       const uint32_t r = base + tid * kBinItems + k;
       if (r < V) {
         offsets[r] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
-        // run table: this rank holds pair m kEmitChunk for each such m in its range
-        for (unsigned long long m = (run + kEmitChunk - 1) / kEmitChunk;
-             m * kEmitChunk < run + c4[k] && m < run_cap; ++m)
+        // run table: this rank holds pair m kEmitTask for each such m in its range
+        for (unsigned long long m = (run + kEmitTask - 1) / kEmitTask;
+             m * kEmitTask < run + c4[k] && m < run_cap; ++m)
           run_first[m] = r;
       }
       run += c4[k];
@@ -315,74 +315,62 @@ struct RowTest {
   }
 };
 
-// Pass 2: every CTA writes whole runs of kEmitChunk consecutive pairs of the
-// chunk, so the work is even however the pairs are spread over splats.
+// Pass 2: every warp takes tasks of kEmitTask consecutive pairs of the chunk
+// (so the work is even however the pairs are spread over splats) and works on
+// its own: it stages the offsets and boxes of the ranks its pairs belong to in
+// its own shared memory, with no barrier shared with the other warps.
 __global__ void __launch_bounds__(kBinThreads, 4) bin_emit_kernel(
     const uint32_t* __restrict__ offsets, const uint2* __restrict__ boxes,
     const SplatRec* __restrict__ rec_sorted, Header* __restrict__ hdr,
     uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals, int gw, int gh,
     int pair_passes, const uint32_t* __restrict__ block_done, uint32_t chunk,
     const uint32_t* __restrict__ run_first, uint32_t run_cap) {
-  __shared__ uint32_t s_off[kEmitChunk + 1];
-  __shared__ uint2 s_box[kEmitChunk + 1];
+  constexpr int kWarps = kBinThreads / 32;
+  __shared__ uint32_t s_offw[kWarps][kEmitTask + 1];
+  __shared__ uint2 s_boxw[kWarps][kEmitTask + 1];
   __shared__ uint32_t s_hist[4][256];
-  __shared__ uint32_t s_unit[kBinThreads / 32][32 * kEmitPer];   // per warp: (rank << 21) | block row
-  __shared__ uint32_t s_iv[kBinThreads / 32][32 * kEmitPer];     // its columns: lo | (hi + 1) << 16
-  __shared__ uint32_t s_r0, s_r1;
-  const int tid = threadIdx.x;
+  __shared__ uint32_t s_unit[kWarps][kEmitTask];   // per warp: (rank << 21) | block row
+  __shared__ uint32_t s_iv[kWarps][kEmitTask];     // its columns: lo | (hi + 1) << 16
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256; i += kBinThreads) (&s_hist[0][0])[i] = 0u;
+  __syncthreads();
   const uint32_t P = hdr->pairs, V = hdr->visible, pbase = hdr->pair_base;
-  const uint32_t nruns = (P + kEmitChunk - 1) / kEmitChunk;
+  const uint32_t ntasks = (P + kEmitTask - 1) / kEmitTask;
   // run-table entries written by the binning's first pass
   const uint32_t nb = (uint32_t)min((unsigned long long)run_cap,
-                                    ((unsigned long long)hdr->pairs_wanted + kEmitChunk - 1) / kEmitChunk);
+                                    ((unsigned long long)hdr->pairs_wanted + kEmitTask - 1) / kEmitTask);
+  uint32_t* s_off = s_offw[warp];
+  uint2* s_box = s_boxw[warp];
   uint32_t live = 0;
-  for (uint32_t c = blockIdx.x; c < nruns; c += gridDim.x) {
-    const uint32_t p0 = pbase + c * kEmitChunk;         // global pair indices [p0, p1)
-    const uint32_t p1 = pbase + min(P, (c + 1) * kEmitChunk);
-    __syncthreads();
-    // the ranks of the run's first and last pairs: from the run table where
-    // it has them (the rank of pair m kEmitChunk; for the last pair, the rank
+  for (uint32_t task = blockIdx.x * kWarps + warp; task < ntasks; task += gridDim.x * kWarps) {
+    const uint32_t p0 = pbase + task * kEmitTask;         // global pair indices [p0, p1)
+    const uint32_t p1 = pbase + min(P, (task + 1) * kEmitTask);
+    // the ranks of the task's first and last pairs: from the run table where it
+    // has them (the rank of pair m kEmitTask; for the last pair, the rank
     // holding the next table pair, an upper bound), else by a warp search
-    if (tid < 32) {
-      const uint32_t m = p0 / kEmitChunk;
-      const uint32_t r = (p0 % kEmitChunk == 0 && m < nb) ? run_first[m]
-                                                          : warp_rank_of_pair(offsets, V, p0, tid);
-      if (tid == 0) s_r0 = r;
-    } else if (tid < 64) {
-      const uint32_t m = (p1 - 1) / kEmitChunk + 1;
-      const uint32_t r = m < nb ? run_first[m] : warp_rank_of_pair(offsets, V, p1 - 1, tid - 32);
-      if (tid == 32) s_r1 = r;
-    }
-    __syncthreads();
-    const uint32_t r0 = s_r0;
-    // ranks overlapping [p0, p1): each has >= 1 pair, so at most kEmitChunk of them
-    const uint32_t nr = min(s_r1 - r0 + 1, (uint32_t)kEmitChunk);
-    for (uint32_t i = tid; i < nr; i += kBinThreads) {
+    const uint32_t m0 = p0 / kEmitTask, m1 = (p1 - 1) / kEmitTask + 1;
+    const uint32_t r0 = (p0 % kEmitTask == 0 && m0 < nb) ? run_first[m0]
+                                                          : warp_rank_of_pair(offsets, V, p0, lane);
+    const uint32_t r1 = m1 < nb ? run_first[m1] : warp_rank_of_pair(offsets, V, p1 - 1, lane);
+    // ranks overlapping [p0, p1): each has >= 1 pair, so at most kEmitTask of
+    // them, and the upper bound adds at most one
+    const uint32_t nr = min(r1 - r0 + 1, (uint32_t)kEmitTask + 1);
+    __syncwarp();   // the previous task is done with the warp's arrays
+    for (uint32_t i = lane; i < nr; i += 32) {
       s_off[i] = offsets[r0 + i];
       s_box[i] = boxes[r0 + i];
     }
-    __syncthreads();
-    // warp w writes the pairs [p0 + 256 w, + 256) in kEmitPer steps of 32
-    // consecutive pairs.  First every pair finds its rank, row and column, and
-    // the first pair of each box row in the range registers the row as a unit;
-    // then each lane tests one unit against the splat's ellipse (RowTest), so
-    // a row costs one test however many blocks it has; then every pair reads
-    // its unit's columns.
-    const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t wp0 = p0 + (uint32_t)warp * (32 * kEmitPer);
-    if (wp0 < p1) {
+    __syncwarp();
+    // The task's pairs in kEmitPer steps of 32 consecutive pairs.  First every
+    // pair finds its rank, row and column, and the first pair of each box row
+    // in the task registers the row as a unit; then each lane tests one unit
+    // against the splat's ellipse (RowTest), so a row costs one test however
+    // many blocks it has; then every pair reads its unit's columns.
+    const uint32_t wp0 = p0;
+    {
       uint32_t unit_mask[kEmitPer], bxy[kEmitPer], lov[kEmitPer];
       uint32_t nunits = 0;
-      // rank of the warp's first pair (the same search on every lane)
-      int lo_base = 0;
-      {
-        int b = (int)nr;
-        while (b - lo_base > 1) {
-          const int mid = (lo_base + b) >> 1;
-          if (s_off[mid] <= wp0) lo_base = mid; else b = mid;
-        }
-      }
+      int lo_base = 0;   // staged rank 0 (r0) holds the task's first pair
 #pragma unroll
       for (int st = 0; st < kEmitPer; ++st) {
         const uint32_t q = wp0 + 32u * st;
@@ -641,7 +629,8 @@ cudaError_t launch_bin_chunk(const uint32_t* offsets, const uint2* boxes,
                                         gw * gh, block_done, done_px, reset_done);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int runs = (int)((pair_cap + kEmitChunk - 1) / kEmitChunk);
+  int runs = (int)((pair_cap + (size_t)kEmitTask * (kBinThreads / 32) - 1) /
+                   ((size_t)kEmitTask * (kBinThreads / 32)));
   if (runs > grid_cap) runs = grid_cap;
   if (runs > emit_resident_ctas()) runs = emit_resident_ctas();
   if (runs < 1) runs = 1;
@@ -658,6 +647,6 @@ cudaError_t launch_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges
 }
 
 size_t bin_tiles(size_t n) { return (n + kBinTile - 1) / kBinTile; }
-size_t emit_run_table(size_t pair_cap) { return pair_cap / kEmitChunk + 2; }
+size_t emit_run_table(size_t pair_cap) { return pair_cap / kEmitTask + 2; }
 
 }  // namespace gsr
