@@ -59,32 +59,21 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
     const uint32_t tile = s_tile;
     if (tile >= ntiles) break;
     const uint32_t base = tile * kBinTile;
-    // gather records into depth order, zero the backward accumulators, count blocks
+    // ids and boxes first: the tile's pair count needs only the boxes, so it is
+    // published before the records move, and later tiles find it sooner
+    uint32_t idv[kBinItems];
+#pragma unroll
+    for (int k = 0; k < kBinItems; ++k) {
+      const uint32_t r = base + k * kBinThreads + tid;
+      idv[k] = r < V ? sorted_ids[r] : 0u;
+    }
 #pragma unroll
     for (int k = 0; k < kBinItems; ++k) {
       const int j = k * kBinThreads + tid;
       const uint32_t r = base + j;
       uint32_t cnt = 0;
-      const uint32_t id = r < V ? sorted_ids[r] : 0u;
-      // the warp's 32 consecutive ranks move their 48-byte records together:
-      // consecutive lanes take consecutive 16-byte words of the 32 records
-      {
-        const uint32_t r0 = r - (uint32_t)lane;
-        const float4* src = reinterpret_cast<const float4*>(rec);
-        float4* dst = reinterpret_cast<float4*>(rec_sorted);
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const int w = t * 32 + lane, q = w / 3, part = w % 3;
-          const uint32_t idq = __shfl_sync(0xffffffffu, id, q);
-          if (r0 + q < V) dst[(size_t)(r0 + q) * 3 + part] = src[(size_t)idq * 3 + part];
-        }
-      }
       if (r < V) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        g2d[3 * (size_t)r] = z;
-        g2d[3 * (size_t)r + 1] = z;
-        g2d[3 * (size_t)r + 2] = z;
-        const uint2 box = boxes_by_id[id];   // every visible splat covers >= 1 block
+        const uint2 box = boxes_by_id[idv[k]];   // every visible splat covers >= 1 block
         boxes[r] = box;
         cnt = (box.y & 0xFFFFu) * (box.y >> 16);
       }
@@ -113,16 +102,38 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
       if (w < warp) wbefore += v;
       total += v;
     }
+    unsigned long long* my = scan_status + tile;
+    const unsigned long long tot = min((unsigned long long)total, kBinCount);
+    if (tid == 0)
+      st_relaxed64(my, ((unsigned long long)tag << 32) | (tile == 0 ? kBinPre : kBinAgg) | tot);
+    // gather the records into depth order and zero the backward accumulators
+    // while lower tiles publish
+#pragma unroll
+    for (int k = 0; k < kBinItems; ++k) {
+      const uint32_t r = base + k * kBinThreads + tid;
+      // the warp's 32 consecutive ranks move their 48-byte records together:
+      // consecutive lanes take consecutive 16-byte words of the 32 records
+      const uint32_t r0 = r - (uint32_t)lane;
+      const float4* src = reinterpret_cast<const float4*>(rec);
+      float4* dst = reinterpret_cast<float4*>(rec_sorted);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int w = t * 32 + lane, q = w / 3, part = w % 3;
+        const uint32_t idq = __shfl_sync(0xffffffffu, idv[k], q);
+        if (r0 + q < V) dst[(size_t)(r0 + q) * 3 + part] = src[(size_t)idq * 3 + part];
+      }
+      if (r < V) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        g2d[3 * (size_t)r] = z;
+        g2d[3 * (size_t)r + 1] = z;
+        g2d[3 * (size_t)r + 2] = z;
+      }
+    }
     // tile offset by decoupled look-back over lower tiles, 32 of them per round
     // trip (lane l reads tile j - l)
     if (warp == 0) {
-      unsigned long long* my = scan_status + tile;
       unsigned long long excl = 0;
-      const unsigned long long tot = min((unsigned long long)total, kBinCount);
-      if (tile == 0) {
-        if (lane == 0) st_relaxed64(my, ((unsigned long long)tag << 32) | kBinPre | tot);
-      } else {
-        if (lane == 0) st_relaxed64(my, ((unsigned long long)tag << 32) | kBinAgg | tot);
+      if (tile > 0) {
         int64_t j = (int64_t)tile - 1;
         uint32_t spins = 0;
         while (j >= 0) {
