@@ -26,7 +26,8 @@
  *     device memory: scratch lives in a caller-allocated workspace
  *     (gs_workspace_size / gs_workspace_init).  One workspace serves one stream
  *     at a time.  gs_render_batch_graph keeps one executable CUDA graph per
- *     workspace (gs_graph_release frees it).
+ *     workspace, and gs_render_batch a second stream and two events per
+ *     workspace (gs_graph_release frees them).
  *   - Parameters are activated values: scales > 0, opacities in [0, 1],
  *     quaternions (w, x, y, z) normalised inside, SH coefficients [N][K][3]
  *     with K = (sh_degree + 1)^2, real orthonormal basis with the
@@ -340,7 +341,9 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
 int gs_render_batch_graph(const gs_request* reqs, int32_t n, gs_workspace* ws,
                           gs_stream_t stream);
 
-/* Frees the executable graph gs_render_batch_graph keeps for ws (if any).  Call
+/* Frees the executable graph gs_render_batch_graph keeps for ws (if any), and
+ * the second stream and two events gs_render_batch creates for ws on first use
+ * (it runs the backward's item ordering on that stream beside the loss).  Call
  * before freeing a workspace's memory that will not be used again. */
 int gs_graph_release(gs_workspace* ws);
 

@@ -52,7 +52,9 @@ cudaError_t launch_raster_bwd(const uint2*, const uint32_t*, const uint32_t*, ui
                               const Header*, uint32_t*, const uint32_t*, const SplatRec*, int, int,
                               int, int, float, int, const void*, const uint32_t*, const float*,
                               float*, int, int, int, float4*, int, int, const float*,
-                              const float*, int, cudaStream_t);
+                              const float*, int, cudaStream_t, int order_done = 0);
+cudaError_t launch_item_order(const uint32_t*, const uint32_t*, const Header*, uint32_t*,
+                              cudaStream_t);
 cudaError_t launch_slab_composite(const void*, int, int, int64_t, float*, float*, float*, float*,
                                   int, cudaStream_t);
 cudaError_t launch_loss(const float*, const float*, int64_t, int, float*, double*, int,
@@ -468,7 +470,8 @@ int raster_fwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
 int raster_bwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
                      const void* state, const uint32_t* last, const float* dL_dimage,
                      int chunk_in, int chunk_out, cudaStream_t st,
-                     const float* t_front = nullptr, const float* behind = nullptr) {
+                     const float* t_front = nullptr, const float* behind = nullptr,
+                     int order_done = 0) {
   int gw, gh;
   blocks_of(cam->width, cam->height, gw, gh);
   const int fin = ws->pair_passes & 1;
@@ -482,8 +485,31 @@ int raster_bwd_stage(gs_workspace* ws, const gs_camera* cam, const gs_raster_opt
                             opts->reduce_threshold > 0 ? opts->reduce_threshold
                                                        : GS_REDUCE_THRESHOLD_DEFAULT,
                             opts->backward_order, at<float4>(ws, L_CHUNK_STATE), chunk_in,
-                            chunk_out, t_front, behind, num_sms(), st),
+                            chunk_out, t_front, behind, num_sms(), st, order_done),
           "raster backward kernel");
+  return GS_OK;
+}
+
+// gs_blend_backward; order_done: the item order was launched already.
+int blend_backward_impl(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
+                        const void* state, const uint32_t* last, const float* dL_dimage,
+                        gs_stream_t stream, int order_done) {
+  int rc = check_bound(ws, cam, opts);
+  if (rc) return rc;
+  if (ws->chunked)
+    return fail(GS_ERR_INVALID_ARG, "memory-efficiency mode: use gs_raster_backward");
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (npix > 0 && (!state || !last || !dL_dimage))
+    return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
+  return raster_bwd_stage(ws, cam, opts, state, last, dL_dimage, 0, 0,
+                          reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, order_done);
+}
+
+// The backward's item order, launched apart (gs_render_batch runs it beside the loss).
+int item_order_stage(gs_workspace* ws, cudaStream_t st) {
+  GS_CUDA(launch_item_order(at<uint32_t>(ws, L_ORDER), at<uint32_t>(ws, L_ITEM_COST),
+                            at<Header>(ws, L_HDR), at<uint32_t>(ws, L_BWD_ITEMS), st),
+          "item order kernel");
   return GS_OK;
 }
 
@@ -546,15 +572,7 @@ int gs_raster_forward(gs_workspace* ws, const gs_camera* cam, const gs_raster_op
 int gs_blend_backward(gs_workspace* ws, const gs_camera* cam, const gs_raster_opts* opts,
                       const void* state, const uint32_t* last, const float* dL_dimage,
                       gs_stream_t stream) {
-  int rc = check_bound(ws, cam, opts);
-  if (rc) return rc;
-  if (ws->chunked)
-    return fail(GS_ERR_INVALID_ARG, "memory-efficiency mode: use gs_raster_backward");
-  const size_t npix = (size_t)cam->width * cam->height;
-  if (npix > 0 && (!state || !last || !dL_dimage))
-    return fail(GS_ERR_INVALID_ARG, "state, last and dL_dimage are required");
-  return raster_bwd_stage(ws, cam, opts, state, last, dL_dimage, 0, 0,
-                          reinterpret_cast<cudaStream_t>(stream));
+  return blend_backward_impl(ws, cam, opts, state, last, dL_dimage, stream, 0);
 }
 
 }  // extern "C"
@@ -611,12 +629,46 @@ int gs_zero_touched_gradients(gs_workspace* ws, int32_t n, float* d_means, float
 }  // extern "C"
 
 namespace {
+// A second stream and two events per workspace, created on first use:
+// gs_render_batch runs the backward's item order on it beside the loss (a
+// fork and join inside its CUDA graph).  Freed by gs_graph_release.
+struct ForkRes {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_fork_mu;
+std::unordered_map<const gs_workspace*, ForkRes> g_forks;
+
+void release_fork(ForkRes& f) {
+  if (f.fork) cudaEventDestroy(f.fork);
+  if (f.join) cudaEventDestroy(f.join);
+  if (f.side) cudaStreamDestroy(f.side);
+  f = ForkRes{};
+}
+
+// The workspace's fork resources, or null (then the caller stays on one stream).
+const ForkRes* fork_res(const gs_workspace* ws) {
+  std::lock_guard<std::mutex> lock(g_fork_mu);
+  ForkRes& f = g_forks[ws];
+  if (!f.side) {
+    if (cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      release_fork(f);
+      g_forks.erase(ws);
+      return nullptr;
+    }
+  }
+  return &f;
+}
+
 int raster_backward_impl(gs_workspace* ws, const float* means, const float* scales,
                          const float* quats, const float* opacities, const float* sh, int32_t n,
                          const gs_camera* cam, const gs_raster_opts* opts, const void* state,
                          const uint32_t* last, const float* dL_dimage, float* d_means,
                          float* d_scales, float* d_quats, float* d_opacities, float* d_sh,
-                         gs_stream_t stream, int store_grads) {
+                         gs_stream_t stream, int store_grads, int order_done = 0) {
   int rc = check_bound(ws, cam, opts);
   if (rc) return rc;
   if (n != ws->n) return fail(GS_ERR_INVALID_ARG, "n differs from the one gs_project was given");
@@ -624,7 +676,7 @@ int raster_backward_impl(gs_workspace* ws, const float* means, const float* scal
                 !d_quats || !d_opacities || !d_sh))
     return fail(GS_ERR_INVALID_ARG, "null parameter or gradient pointer");
   if (!ws->chunked) {
-    rc = gs_blend_backward(ws, cam, opts, state, last, dL_dimage, stream);
+    rc = blend_backward_impl(ws, cam, opts, state, last, dL_dimage, stream, order_done);
   } else {
     // memory-efficiency mode: the chunks again, front to back, (C', T) carried
     // between them; the pair buffers hold one chunk, so each is binned anew
@@ -761,15 +813,25 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
     if (!rc) rc = gs_raster_forward(ws, &q.camera, &q.opts, q.image, q.state, q.last, q.n_contrib, stream);
     if (!rc && q.mode == GS_MODE_FORWARD_BACKWARD) {
       const int64_t nv = (int64_t)q.camera.width * q.camera.height * 3;
+      // the backward's item order needs only the forward: it runs beside the loss
+      const ForkRes* f = (q.loss_kind != GS_LOSS_NONE && !ws->chunked) ? fork_res(ws) : nullptr;
+      if (f) {
+        GS_CUDA(cudaEventRecord(f->fork, st), "fork event");
+        GS_CUDA(cudaStreamWaitEvent(f->side, f->fork, 0), "fork wait");
+        rc = item_order_stage(ws, f->side);
+        if (rc) return rc;
+        GS_CUDA(cudaEventRecord(f->join, f->side), "join event");
+      }
       if (q.loss_kind != GS_LOSS_NONE) {
         if (!q.image) return fail(GS_ERR_INVALID_ARG, "request %d: a loss needs the image", i);
         rc = gs_loss(q.image, q.target, nv, q.loss_kind, q.dL_dimage, q.loss, stream);
       }
+      if (f) GS_CUDA(cudaStreamWaitEvent(st, f->join, 0), "join wait");
       if (!rc)
         rc = raster_backward_impl(ws, q.scene.means, q.scene.scales, q.scene.quats,
                                   q.scene.opacities, q.scene.sh, q.scene.n, &q.camera, &q.opts,
                                   q.state, q.last, q.dL_dimage, q.d_means, q.d_scales, q.d_quats,
-                                  q.d_opacities, q.d_sh, stream, store);
+                                  q.d_opacities, q.d_sh, stream, store, f != nullptr);
       if (!rc && q.loss_host && q.loss_kind != GS_LOSS_NONE)
         GS_CUDA(cudaMemcpyAsync(q.loss_host, q.loss, sizeof(double), cudaMemcpyDeviceToHost,
                                 reinterpret_cast<cudaStream_t>(stream)),
@@ -811,6 +873,12 @@ int gs_render_batch_graph(const gs_request* reqs, int32_t n, gs_workspace* ws,
     }
   }
   if (direct) return gs_render_batch(reqs, n, ws, stream);
+  // the second stream of the item-order fork is created outside the capture
+  for (int i = 0; i < n; ++i)
+    if (reqs[i].mode == GS_MODE_FORWARD_BACKWARD && reqs[i].loss_kind != GS_LOSS_NONE) {
+      fork_res(ws);
+      break;
+    }
   GS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
   rc = gs_render_batch(reqs, n, ws, stream);
   cudaGraph_t graph = nullptr;
@@ -842,11 +910,19 @@ int gs_render_batch_graph(const gs_request* reqs, int32_t n, gs_workspace* ws,
 }
 
 int gs_graph_release(gs_workspace* ws) {
-  std::lock_guard<std::mutex> lock(g_graph_mu);
-  auto it = g_graphs.find(ws);
-  if (it != g_graphs.end()) {
-    if (it->second) cudaGraphExecDestroy(it->second);
-    g_graphs.erase(it);
+  {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    auto it = g_graphs.find(ws);
+    if (it != g_graphs.end()) {
+      if (it->second) cudaGraphExecDestroy(it->second);
+      g_graphs.erase(it);
+    }
+  }
+  std::lock_guard<std::mutex> lock(g_fork_mu);
+  auto f = g_forks.find(ws);
+  if (f != g_forks.end()) {
+    release_fork(f->second);
+    g_forks.erase(f);
   }
   return GS_OK;
 }

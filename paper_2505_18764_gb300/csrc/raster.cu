@@ -1069,6 +1069,13 @@ cudaError_t launch_raster_fwd(const uint2* ranges, const uint32_t* items, const 
   return cudaGetLastError();
 }
 
+// The backward's item order (costliest first) from the forward's item times.
+cudaError_t launch_item_order(const uint32_t* fwd_items, const uint32_t* item_cost,
+                              const Header* hdr, uint32_t* items, cudaStream_t st) {
+  item_order_kernel<<<1, kOrderThreads, 0, st>>>(fwd_items, item_cost, hdr, items);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
                               const uint32_t* item_cost, uint32_t* items, const Header* hdr,
                               uint32_t* next, const uint32_t* pair_ranks, const SplatRec* rec,
@@ -1076,13 +1083,16 @@ cudaError_t launch_raster_bwd(const uint2* ranges, const uint32_t* fwd_items,
                               const void* state, const uint32_t* last, const float* dLdC,
                               float* g2d, int mode, int threshold, int back, float4* chunk_state,
                               int chunk_in, int chunk_out, const float* t_front,
-                              const float* behind, int num_sms, cudaStream_t st) {
+                              const float* behind, int num_sms, cudaStream_t st,
+                              int order_done) {
   if (gw * gh == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  item_order_kernel<<<1, kOrderThreads, 0, st>>>(fwd_items, item_cost, hdr, items);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (!order_done) {   // else launch_item_order ran already (on another stream)
+    item_order_kernel<<<1, kOrderThreads, 0, st>>>(fwd_items, item_cost, hdr, items);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (mode == GS_REDUCE_NAIVE) {
     static const int per_sm = resident_per_sm(raster_bwd_kernel<GS_REDUCE_NAIVE>);
     const int grid = per_sm * num_sms;
