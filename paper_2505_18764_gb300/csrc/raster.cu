@@ -234,7 +234,54 @@ __device__ __forceinline__ uint32_t fwd_item(FwdRing& R, const SplatRec* __restr
   const uint32_t beg = range.x, end = range.y;
   if (beg < end) ring_start(R, rec, pair_ranks, beg, end, lane);
   int slot = 0;
-  for (uint32_t gs = beg; gs < end; gs += 32u, slot = (slot + 1) & (kFwdStages - 1)) {
+  if (COLS == 4) {
+    // 4x4 cells (long lists): two groups per round, so the round's fixed work
+    // (waits, active rectangle, votes, refills) is spread over 64 entries
+    auto walk = [&](int s, uint32_t m) {
+      while (m) {
+        const int j1 = __ffs(m) - 1;
+        m &= m - 1u;
+        const bool two = m != 0u;
+        const int j2 = two ? __ffs(m) - 1 : j1;
+        if (two) m &= m - 1u;
+        const float4 a1 = R.a[s][j1], b1 = R.b[s][j1];
+        const float4 a2 = R.a[s][j2], b2 = R.b[s][j2];
+        float y1, y2;
+        const float qa1 = frag_q(px, pya, a1, b1, y1, y2);
+        const float qa2 = frag_q(px, pya, a2, b2, y1, y2);
+        const float4 c1 = R.c[s][j1], c2 = R.c[s][j2];
+        const uint32_t rank1 = R.rank[s][j1], rank2 = R.rank[s][j2];
+        float G, at;
+        const float alpha1 = frag_alpha(c1.w, qa1, G, at), alpha2 = frag_alpha(c2.w, qa2, G, at);
+        if (!pa.done && qa1 <= b1.y) blend(pa, true, alpha1, c1, rank1, t_cull);
+        if (two && !pa.done && qa2 <= b2.y) blend(pa, true, alpha2, c2, rank2, t_cull);
+      }
+    };
+    for (uint32_t gs = beg; gs < end; gs += 64u, slot ^= 2) {
+      const uint32_t ip0 = gs + 32u * kFwdStages + lane, ip1 = ip0 + 32u;
+      const uint32_t rk0 = ip0 < end ? __ldg(pair_ranks + ip0) : 0u;
+      const uint32_t rk1 = ip1 < end ? __ldg(pair_ranks + ip1) : 0u;
+      cp_async_wait_group<kFwdStages - 2>();
+      __syncwarp();
+      if (__all_sync(kFull, pa.done)) break;
+      const uint32_t cnt0 = min(32u, end - gs);
+      const uint32_t cnt1 = gs + 32u < end ? min(32u, end - gs - 32u) : 0u;
+      float rx, ry, rw, rh;
+      active_rect(!pa.done, false, x, ya, yb, rx, ry, rw, rh);
+      const uint32_t m0 = __ballot_sync(kFull, (uint32_t)lane < cnt0 &&
+                                                   rect_may_hit(R.a[slot][lane], R.b[slot][lane],
+                                                                rx, ry, rw, rh));
+      const uint32_t m1 = __ballot_sync(kFull, (uint32_t)lane < cnt1 &&
+                                                   rect_may_hit(R.a[slot + 1][lane],
+                                                                R.b[slot + 1][lane], rx, ry, rw, rh));
+      walk(slot, m0);
+      walk(slot + 1, m1);
+      __syncwarp();   // every lane is done with both slots before they are refilled
+      ring_issue(R, slot, rec, ip0, end, rk0, lane);
+      ring_issue(R, slot + 1, rec, ip1, end, rk1, lane);
+    }
+  }
+  for (uint32_t gs = COLS == 4 ? end : beg; gs < end; gs += 32u, slot = (slot + 1) & (kFwdStages - 1)) {
     const uint32_t ip = gs + 32u * kFwdStages + lane;      // this lane's entry of the refill
     const uint32_t rk_next = ip < end ? __ldg(pair_ranks + ip) : 0u;
     cp_async_wait_group<kFwdStages - 1>();
