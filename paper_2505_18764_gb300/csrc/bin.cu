@@ -36,6 +36,8 @@ constexpr unsigned long long kBinCount = (1ull << 30) - 1;
 constexpr int kEmitPer = 8;                   // steps of 32 pairs in one warp task
 constexpr int kEmitTask = 32 * kEmitPer;       // pairs of one warp task of the emission (256)
 constexpr int kChunkWhole = 0, kChunkBudget = 1, kChunkSlab = 2;   // chunk_setup_kernel modes
+static_assert(kChunkWhole == 0 && kChunkBudget == 1,
+              "the whole-view and budget modes are the workspace's chunked flag (0 or 1)");
 
 // Pass 1: one tile of 1024 depth ranks per step of a persistent loop.
 __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(
