@@ -19,10 +19,12 @@ cudaError_t launch_project_fwd(const float*, const float*, const float*, const f
 cudaError_t launch_project_bwd(const float*, const float*, const float*, const float*, const float*,
                                int, int, const gs_camera&, int, const uint32_t*, const float*,
                                const Header*, float*, float*, float*, float*, float*, int,
-                               cudaStream_t, int);
+                               cudaStream_t, int, uint32_t*, uint32_t*);
+cudaError_t launch_zero_listed(int, int, const uint32_t*, const uint32_t*, float*, float*, float*,
+                               float*, float*, int, cudaStream_t);
 cudaError_t launch_copy_word(const uint32_t*, uint32_t*, cudaStream_t);
 cudaError_t launch_zero_left(int, int, const uint32_t*, const uint32_t*, const uint32_t*, float*,
-                             float*, float*, float*, float*, int, cudaStream_t);
+                             float*, float*, float*, float*, int, cudaStream_t, const uint32_t*);
 cudaError_t launch_zero_touched(int, int, const uint32_t*, const Header*, float*, float*, float*,
                                 float*, float*, int, cudaStream_t);
 cudaError_t launch_onesweep_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,
@@ -115,8 +117,9 @@ enum Slot {
   L_BOXES_ID,    // [n] uint2 16x16-block box of each splat, by splat id
   L_REC_SORTED,  // [n] records by depth rank
   L_G2D,         // [n][12] backward accumulators by depth rank
-  L_OFFSETS,     // [n] first pair index of each depth rank, then the emission's run table:
-                 // [pair_cap / 2048 + 2] the rank holding pair m * 2048
+  L_OFFSETS,     // [n] first pair index of each depth rank, then the emission's run table
+                 // ([pair_cap / 256 + 2] the rank holding pair m * 256), then [n] the ids
+                 // whose gradient rows the last store-mode backward wrote
   L_BOXES,       // [n] uint2 block box of each depth rank
   L_CHUNK_STATE, // memory-efficiency mode: [width_cap * height_cap] float4 (g.C', T) between
                  // chunks, then [2 blocks_cap] u32: the chunk after which each block's pixels
@@ -156,7 +159,7 @@ bool compute_layout(int64_t n_cap, int w_cap, int h_cap, int64_t pair_cap, int c
   sz[L_KEYS] = n_cap * 4;
   sz[L_KA] = sz[L_VA] = sz[L_KB] = sz[L_VB] = n_cap * 4;
   sz[L_REC] = sz[L_REC_SORTED] = sz[L_G2D] = n_cap * sizeof(SplatRec);
-  sz[L_OFFSETS] = (n_cap + emit_run_table(pair_cap)) * 4;
+  sz[L_OFFSETS] = (2 * n_cap + emit_run_table(pair_cap)) * 4;
   sz[L_BOXES_ID] = n_cap * 8;
   sz[L_BOXES] = n_cap * 8;
   sz[L_CHUNK_STATE] = chunked ? (size_t)w_cap * h_cap * 16 + blocks * 2 * 4 : 0;
@@ -505,6 +508,14 @@ int blend_backward_impl(gs_workspace* ws, const gs_camera* cam, const gs_raster_
                           reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, order_done);
 }
 
+// The ids whose gradient rows the last store-mode backward projection wrote,
+// and its state in the epoch words: [0] their count, [1] 1 while the list
+// covers every non-zero gradient row (a backward projection that adds clears it).
+uint32_t* live_list(gs_workspace* ws) {
+  return at<uint32_t>(ws, L_OFFSETS) + ws->n_cap + emit_run_table(ws->pair_cap);
+}
+uint32_t* list_state(gs_workspace* ws) { return at<uint32_t>(ws, L_EPOCH) + 2; }
+
 // The backward's item order, launched apart (gs_render_batch runs it beside the loss).
 int item_order_stage(gs_workspace* ws, cudaStream_t st) {
   GS_CUDA(launch_item_order(at<uint32_t>(ws, L_ORDER), at<uint32_t>(ws, L_ITEM_COST),
@@ -591,11 +602,23 @@ int project_backward_impl(gs_workspace* ws, const float* means, const float* sca
   if (n > 0 && (!means || !scales || !quats || !opacities || !sh || !d_means || !d_scales ||
                 !d_quats || !d_opacities || !d_sh))
     return fail(GS_ERR_INVALID_ARG, "null parameter or gradient pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t* ls = list_state(ws);
+  if (store_grads) {
+    // with a valid list, the rows the last store-mode view wrote are the only
+    // non-zero ones: zero them, then start this view's list
+    GS_CUDA(launch_zero_listed(ws->n, ws->sh_degree, live_list(ws), ls, d_means, d_scales, d_quats,
+                               d_opacities, d_sh, num_sms(), st),
+            "listed-rows zeroing kernel");
+    GS_CUDA(cudaMemsetAsync(ls, 0, sizeof(uint32_t), st), "list count reset");
+  }
   GS_CUDA(launch_project_bwd(means, scales, quats, opacities, sh, ws->n, ws->sh_degree, *cam,
                              ws->clamp01, at<uint32_t>(ws, L_VB), at<float>(ws, L_G2D),
                              at<Header>(ws, L_HDR), d_means, d_scales, d_quats, d_opacities, d_sh,
-                             num_sms(), reinterpret_cast<cudaStream_t>(stream), store_grads),
+                             num_sms(), st, store_grads, live_list(ws), ls),
           "projection backward kernel");
+  // store: the list now holds every row this view wrote; add: it no longer covers them
+  GS_CUDA(launch_set_word(ls + 1, store_grads ? 1u : 0u, st), "list state");
   return GS_OK;
 }
 }  // namespace
@@ -807,7 +830,7 @@ int gs_render_batch(const gs_request* reqs, int32_t n, gs_workspace* ws, gs_stre
     if (!rc && store)   // rows of the splats that left the view (before the sort replaces the order)
       GS_CUDA(launch_zero_left(q.scene.n, q.scene.sh_degree, at<uint32_t>(ws, L_VB),
                                at<uint32_t>(ws, L_EPOCH) + 1, at<uint32_t>(ws, L_KEYS), q.d_means,
-                               q.d_scales, q.d_quats, q.d_opacities, q.d_sh, num_sms(), st),
+                               q.d_scales, q.d_quats, q.d_opacities, q.d_sh, num_sms(), st, list_state(ws)),
               "gradient zeroing kernel");
     if (!rc) rc = gs_sort(ws, stream);
     if (!rc) rc = gs_raster_forward(ws, &q.camera, &q.opts, q.image, q.state, q.last, q.n_contrib, stream);

@@ -587,11 +587,18 @@ __device__ __forceinline__ void project_bwd_batch(
     const float* __restrict__ sh, bool sh_vec, bool dq_vec, const CamDev& cam, int clamp01,
     const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ g2d,
     float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_opac, float* __restrict__ d_sh) {
+    float* __restrict__ d_opac, float* __restrict__ d_sh, uint32_t* __restrict__ live_list,
+    uint32_t* __restrict__ list_state) {
   using Row = BwdRow<DEG>;
   constexpr int P = Row::kPitch;
   const bool mine = lane < count;
   const uint32_t id = mine ? sorted_ids[r] : 0u;
+  if (STORE) {   // the rows this view writes: the next store-mode view zeroes them first
+    uint32_t at0 = 0;
+    if (lane == 0) at0 = atomicAdd(&list_state[0], (uint32_t)count);
+    at0 = __shfl_sync(0xffffffffu, at0, 0);
+    if (mine) live_list[at0 + lane] = id;
+  }
   float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, quat = ga;
   float gop = 0.f;
   if (mine) {
@@ -663,8 +670,11 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
     CamDev cam, int clamp01, const uint32_t* __restrict__ sorted_ids,
     const float4* __restrict__ g2d, const Header* __restrict__ hdr, float* __restrict__ d_means,
     float* __restrict__ d_scales, float* __restrict__ d_quats, float* __restrict__ d_opac,
-    float* __restrict__ d_sh) {
+    float* __restrict__ d_sh, uint32_t* __restrict__ live_list, uint32_t* __restrict__ list_state) {
   constexpr int P = BwdRow<DEG>::kPitch;
+  // STORE with a valid list: every non-zero row was on it and has been zeroed
+  // (zero_listed_kernel), so the rows without a gradient need nothing
+  const bool zero_nonlive = STORE && list_state[1] == 0u;
   __shared__ __align__(16) float s_rows[kProjBwdWarps][32 * P];
   __shared__ uint32_t s_queue[kProjBwdWarps][64];
   const int lane = threadIdx.x & 31;
@@ -684,7 +694,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
              gb.y != 0.f || gb.z != 0.f || gb.w != 0.f || g[12 * r + 8] != 0.f;
     }
     const unsigned m = __ballot_sync(0xffffffffu, live);
-    if (STORE) {   // rows of visible splats without a gradient: zeros
+    if (zero_nonlive) {   // rows of visible splats without a gradient: zeros
       const unsigned z = __ballot_sync(0xffffffffu, r < V && !live);
       if (z) {
         const uint32_t zid = (z >> lane) & 1u ? sorted_ids[r] : 0u;
@@ -703,13 +713,13 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
       queued -= 32;
       project_bwd_batch<DEG, STORE>(rows, queue[queued + lane], 32, lane, means, scales, quats,
                                     sh, sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d, d_means,
-                                    d_scales, d_quats, d_opac, d_sh);
+                                    d_scales, d_quats, d_opac, d_sh, live_list, list_state);
     }
   }
   if (queued > 0)
     project_bwd_batch<DEG, STORE>(rows, lane < queued ? queue[lane] : 0u, queued, lane, means,
                                   scales, quats, sh, sh_vec, dq_vec, cam, clamp01, sorted_ids, g2d,
-                                  d_means, d_scales, d_quats, d_opac, d_sh);
+                                  d_means, d_scales, d_quats, d_opac, d_sh, live_list, list_state);
 }
 
 // Zeroing of the gradient rows of the last depth order's splats (the rows a
@@ -784,7 +794,8 @@ __global__ void __launch_bounds__(256) zero_left_kernel(
     const uint32_t* __restrict__ prev_sorted_ids, const uint32_t* __restrict__ prev_V,
     const uint32_t* __restrict__ keys, uint32_t n, int sh_vec, int dq_vec,
     float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_opac, float* __restrict__ d_sh) {
+    float* __restrict__ d_opac, float* __restrict__ d_sh, const uint32_t* __restrict__ list_state) {
+  if (list_state[1] != 0u) return;   // a valid list covers these rows (zero_listed_kernel)
   const uint32_t V = min(*prev_V, n);
   const int lane = threadIdx.x & 31;
   for (uint32_t base = blockIdx.x * 256u + (threadIdx.x & ~31u); base < V;
@@ -793,6 +804,30 @@ __global__ void __launch_bounds__(256) zero_left_kernel(
     uint32_t id = r < V ? prev_sorted_ids[r] : 0u;
     const bool left = r < V && id < n && keys[id] == kNone;
     const unsigned z = __ballot_sync(0xffffffffu, left);
+    if (!z) continue;
+    const int cnt = __popc(z);
+    const int src = lane < cnt ? (int)__fns(z, 0u, lane + 1) : 0;
+    id = __shfl_sync(0xffffffffu, id, src);
+    zero_splat_rows<DEG>(id, cnt, lane, sh_vec, dq_vec, d_means, d_scales, d_quats, d_opac, d_sh);
+  }
+}
+
+// The rows of the splats the last store-mode view wrote (live_list), zeroed
+// before this view's are written: with a valid list (list_state[1]) those are
+// the only rows that can be non-zero.
+template <int DEG>
+__global__ void __launch_bounds__(256) zero_listed_kernel(
+    const uint32_t* __restrict__ live_list, const uint32_t* __restrict__ list_state, uint32_t n,
+    int sh_vec, int dq_vec, float* __restrict__ d_means, float* __restrict__ d_scales,
+    float* __restrict__ d_quats, float* __restrict__ d_opac, float* __restrict__ d_sh) {
+  if (list_state[1] == 0u) return;
+  const uint32_t count = min(list_state[0], n);
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = blockIdx.x * 256u + (threadIdx.x & ~31u); base < count;
+       base += gridDim.x * 256u) {
+    const uint32_t r = base + lane;
+    uint32_t id = r < count ? live_list[r] : 0u;
+    const unsigned z = __ballot_sync(0xffffffffu, r < count && id < n);   // (ids of this scene)
     if (!z) continue;
     const int cnt = __popc(z);
     const int src = lane < cnt ? (int)__fns(z, 0u, lane + 1) : 0;
@@ -851,7 +886,8 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
                                const gs_camera& cam, int clamp01, const uint32_t* sorted_ids,
                                const float* g2d, const Header* hdr, float* d_means,
                                float* d_scales, float* d_quats, float* d_opac, float* d_sh,
-                               int num_sms, cudaStream_t st, int store) {
+                               int num_sms, cudaStream_t st, int store, uint32_t* live_list,
+                               uint32_t* list_state) {
   (void)opac;
   int blocks = (n_cap + kProjBwdThreads - 1) / kProjBwdThreads;
   if (blocks == 0) return cudaSuccess;
@@ -865,11 +901,11 @@ cudaError_t launch_project_bwd(const float* means, const float* scales, const fl
   if (store)                                                                                   \
     project_bwd_kernel<D, true><<<blocks, kProjBwdThreads, 0, st>>>(                           \
         means, scales, q4, sh, sh_vec, dq_vec, cd, clamp01, sorted_ids, g4, hdr, d_means,      \
-        d_scales, d_quats, d_opac, d_sh);                                                      \
+        d_scales, d_quats, d_opac, d_sh, live_list, list_state);                               \
   else                                                                                         \
     project_bwd_kernel<D, false><<<blocks, kProjBwdThreads, 0, st>>>(                          \
         means, scales, q4, sh, sh_vec, dq_vec, cd, clamp01, sorted_ids, g4, hdr, d_means,      \
-        d_scales, d_quats, d_opac, d_sh)
+        d_scales, d_quats, d_opac, d_sh, live_list, list_state)
   switch (deg) {
     case 0: GS_PROJECT_BWD(0); break;
     case 1: GS_PROJECT_BWD(1); break;
@@ -888,7 +924,7 @@ cudaError_t launch_copy_word(const uint32_t* src, uint32_t* dst, cudaStream_t st
 cudaError_t launch_zero_left(int n, int deg, const uint32_t* prev_sorted_ids,
                              const uint32_t* prev_V, const uint32_t* keys, float* d_means,
                              float* d_scales, float* d_quats, float* d_opac, float* d_sh,
-                             int num_sms, cudaStream_t st) {
+                             int num_sms, cudaStream_t st, const uint32_t* list_state) {
   int blocks = (n + 255) / 256;
   if (blocks == 0) return cudaSuccess;
   if (blocks > num_sms * 8) blocks = num_sms * 8;
@@ -897,7 +933,7 @@ cudaError_t launch_zero_left(int n, int deg, const uint32_t* prev_sorted_ids,
 #define GS_ZERO_LEFT(D)                                                                         \
   zero_left_kernel<D><<<blocks, 256, 0, st>>>(prev_sorted_ids, prev_V, keys, (uint32_t)n,       \
                                               sh_vec, dq_vec, d_means, d_scales, d_quats, d_opac, \
-                                              d_sh)
+                                              d_sh, list_state)
   switch (deg) {
     case 0: GS_ZERO_LEFT(0); break;
     case 1: GS_ZERO_LEFT(1); break;
@@ -905,6 +941,28 @@ cudaError_t launch_zero_left(int n, int deg, const uint32_t* prev_sorted_ids,
     default: GS_ZERO_LEFT(3); break;
   }
 #undef GS_ZERO_LEFT
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_listed(int n, int deg, const uint32_t* live_list,
+                               const uint32_t* list_state, float* d_means, float* d_scales,
+                               float* d_quats, float* d_opac, float* d_sh, int num_sms,
+                               cudaStream_t st) {
+  int blocks = (n + 255) / 256;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > num_sms * 8) blocks = num_sms * 8;
+  const int sh_vec = ((uintptr_t)d_sh & 15) == 0;
+  const int dq_vec = ((uintptr_t)d_quats & 15) == 0;
+#define GS_ZERO_LISTED(D)                                                                       \
+  zero_listed_kernel<D><<<blocks, 256, 0, st>>>(live_list, list_state, (uint32_t)n, sh_vec,      \
+                                                dq_vec, d_means, d_scales, d_quats, d_opac, d_sh)
+  switch (deg) {
+    case 0: GS_ZERO_LISTED(0); break;
+    case 1: GS_ZERO_LISTED(1); break;
+    case 2: GS_ZERO_LISTED(2); break;
+    default: GS_ZERO_LISTED(3); break;
+  }
+#undef GS_ZERO_LISTED
   return cudaGetLastError();
 }
 

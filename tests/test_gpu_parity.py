@@ -519,6 +519,36 @@ def test_render_batch_zero_touched_and_host_loss_in_a_graph(mode):
     ws.release_graph()
 
 
+def test_store_mode_after_an_adding_backward():
+    """zero_touched 2 zeroes only the rows the last store-mode view wrote; a
+    backward that adds in between (zero_touched 0) makes it fall back to zeroing
+    every row the last depth order held.  Either way each view ends with its
+    own gradients alone."""
+    scene_np, _ = syn.precision_sweep_views(1)
+    cams = [syn.orbit_camera(a, 2.2, 35.0, 96, 80) for a in (0.0, 2.6, 1.3, 4.0)]
+    opts = gs.RasterOpts()
+    scene = gs.SceneTensors.from_numpy(scene_np)
+    ws = gs.Workspace(scene.n, cams[0].width, cams[0].height, opts)
+    grads = gs.zero_grads(scene)
+    for i, (cam, mode) in enumerate(zip(cams, (2, 0, 2, 2))):
+        tgt = torch.rand((cam.height, cam.width, 3), device="cuda")
+        if mode == 0:
+            for g in grads.values():
+                g.zero_()
+        rq = gs.Request(scene, cam, opts, backward=True, loss_kind="l2", target=tgt,
+                        outputs=dict(grads=grads), zero_touched=mode)
+        gs.render_batch([rq], ws)
+        fresh = gs.Request(scene, cam, opts, backward=True, loss_kind="l2", target=tgt)
+        gs.render_batch([fresh], gs.Workspace(scene.n, cam.width, cam.height, opts))
+        torch.cuda.synchronize()
+        gs.check_status(ws)
+        for k in GROUPS:
+            a = grads[k].cpu().numpy().astype(np.float64)
+            b = fresh.outputs["grads"][k].cpu().numpy().astype(np.float64)
+            assert rel_l2(a, b) < 1e-5, (i, k)
+            assert np.all(a[np.all(b.reshape(b.shape[0], -1) == 0, axis=1)] == 0), (i, k)
+
+
 def test_render_batch_graph_matches_direct():
     """The graph form of render_batch gives the direct form's results on its
     first call (run directly), its second (captured and instantiated), with a
