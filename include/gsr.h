@@ -172,11 +172,14 @@ typedef struct gs_request {
                             views: 0 = gradients are added to d_* (the default); 1 = first zero
                             the rows the workspace's last depth order touched
                             (gs_zero_touched_gradients), then add; 2 = d_* end up holding this
-                            view's gradient alone: the visible splats' rows are written (zeros
-                            where a splat gets no gradient) and the rows of splats the last depth
-                            order held but this view culls are zeroed.  2 needs d_* to hold
-                            zeros or the previous request's gradients of the same scene on this
-                            workspace, and saves the reset pass and the read of the rows */
+                            view's gradient alone: the rows the last store-mode request on this
+                            workspace wrote are zeroed (the workspace keeps their ids), then the
+                            rows of this view's splats with a gradient are written.  If a
+                            backward that adds ran in between, every row the last depth order
+                            held and every visible splat's row is zeroed or written instead.
+                            2 needs d_* to hold zeros or the previous request's gradients of the
+                            same scene on this workspace, and saves the reset pass and the read
+                            of the rows */
   int32_t pad0;
   double* loss_host;     /* may be null: the loss is also copied to this pinned host double at
                             the end of the request (inside the batch's CUDA graph) */
