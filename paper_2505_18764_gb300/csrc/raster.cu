@@ -222,7 +222,6 @@ __device__ __forceinline__ uint32_t fwd_item(FwdRing& R, const SplatRec* __restr
   lane_pixels<COLS>(x0, y0, lane, x, ya, own);
   const int yb = ya + 4;
   const float px = (float)x + 0.5f, pya = (float)ya + 0.5f, pyb = (float)yb + 0.5f;
-  const float xs = (float)x0 + 0.5f, ys = (float)y0 + 0.5f;
   PixelFwd pa{1.f, 0.f, 0.f, 0.f, kNone, 0u, !(own && x < W && ya < H)};
   PixelFwd pb{1.f, 0.f, 0.f, 0.f, kNone, 0u, NPX == 1 || !(x < W && yb < H)};
   if (resume) {
@@ -537,42 +536,61 @@ __device__ __forceinline__ void load_pixel_bwd(PixelBwd& p, bool valid, int x, i
   }
 }
 
-// One fragment of Procedure 1 plus the chain rule to the 2D parameters; the
-// nine values go to v.  The pixel's fragments are exactly the hits below its
-// end rank: the forward stopped after the fragment that took T under t_cull,
-// so Procedure 1's cull test needs no second evaluation.  A missed pixel (hit
+// One fragment of Procedure 1 plus the chain rule to the 2D parameters, in two
+// halves.  frag_pre takes what does not depend on the pixel's running state
+// (alpha, 1 / (1 - alpha), g . c, the whitened offset z), frag_post the rest:
+// the two halves of two candidates can then be interleaved, the second
+// candidate's first half filling the first candidate's latencies.  The nine
+// values go to v.  The pixel's fragments are exactly the hits below its end
+// rank: the forward stopped after the fragment that took T under t_cull, so
+// Procedure 1's cull test needs no second evaluation.  A missed pixel (hit
 // false) runs the same code with G = 0: every term is an exact zero and the
 // state is unchanged.
-__device__ __forceinline__ void grad_fragment(PixelBwd& p, bool hit, float q, float y1, float y2,
-                                              const float4& a, const float4& b, const float4& c,
-                                              float v[9]) {
-  float G, at;
-  const float alpha = frag_alpha_masked(hit, c.w, q, G, at);
-  const float oma = __fsub_rn(1.0f, alpha);
-  const float wT = alpha * p.T;
+struct FragPre {
+  float G, at, alpha, oma, inv, gc, z0, z1;
+};
+
+__device__ __forceinline__ void frag_pre(const PixelBwd& p, bool hit, float q, float y1, float y2,
+                                         const float4& a, const float4& b, const float4& c,
+                                         FragPre& r) {
+  r.alpha = frag_alpha_masked(hit, c.w, q, r.G, r.at);
+  r.oma = __fsub_rn(1.0f, r.alpha);
+  r.inv = __fdividef(1.0f, r.oma);
+  r.gc = p.g0 * c.x + p.g1 * c.y + p.g2 * c.z;
+  // z = Sigma^-1 d = L^-T L^-1 d, in units of 1 / (2 ln 2):
+  // dpower/dmu_2D = z and dpower/dSigma_2D = z z^T / 2
+  r.z1 = b.x * y2;
+  r.z0 = a.z * y1 - a.w * r.z1;
+}
+
+__device__ __forceinline__ void frag_post(PixelBwd& p, const FragPre& r, float v[9]) {
+  const float wT = r.alpha * p.T;
   // Eq. 3
   v[5] = p.g0 * wT;
   v[6] = p.g1 * wT;
   v[7] = p.g2 * wT;
   // Eq. 7 with D_i = g . C'_i before its update, then Eq. 6 and Eq. 5
-  const float gc = p.g0 * c.x + p.g1 * c.y + p.g2 * c.z;
-  const float dLda = (p.T * gc - p.D) * __fdividef(1.0f, oma);
-  p.D -= wT * gc;
-  p.T = next_T(p.T, alpha);
+  const float dLda = (p.T * r.gc - p.D) * r.inv;
+  p.D -= wT * r.gc;
+  p.T = next_T(p.T, r.alpha);
   // alpha = min(0.99, o G): no gradient through the clamp
-  const float d_at = at < kAlphaMax ? dLda : 0.f;
-  v[8] = G * d_at;
-  // z = Sigma^-1 d = L^-T L^-1 d, in units of 1 / (2 ln 2):
-  // dpower/dmu_2D = z and dpower/dSigma_2D = z z^T / 2
-  const float w = at * d_at;
-  const float z1 = b.x * y2;
-  const float z0 = a.z * y1 - a.w * z1;
-  const float wz0 = w * z0, wz1 = w * z1;
+  const float d_at = r.at < kAlphaMax ? dLda : 0.f;
+  v[8] = r.G * d_at;
+  const float w = r.at * d_at;
+  const float wz0 = w * r.z0, wz1 = w * r.z1;
   v[0] = wz0;
   v[1] = wz1;
-  v[2] = wz0 * z0;
-  v[3] = wz0 * z1;
-  v[4] = wz1 * z1;
+  v[2] = wz0 * r.z0;
+  v[3] = wz0 * r.z1;
+  v[4] = wz1 * r.z1;
+}
+
+__device__ __forceinline__ void grad_fragment(PixelBwd& p, bool hit, float q, float y1, float y2,
+                                              const float4& a, const float4& b, const float4& c,
+                                              float v[9]) {
+  FragPre r;
+  frag_pre(p, hit, q, y1, y2, a, b, c, r);
+  frag_post(p, r, v);
 }
 
 // One warp, one footprint COLS x 4 with one pixel per lane (COLS = 8 or 4).
@@ -608,20 +626,41 @@ __device__ __forceinline__ void bwd_item(BwdRing& R, GradBatch& B,
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
                                                        (float)(COLS - 1), 3.f));
+    // Two candidates per step (the second may be absent): both are tested, then
+    // the first halves of both fragments are taken before the second halves,
+    // which follow the depth order.
     while (m) {
-      const int j = __ffs(m) - 1;
+      const int j0 = __ffs(m) - 1;
       m &= m - 1u;
-      const uint32_t rank = R.rank[slot][j];
-      const float4 a = R.a[slot][j];
-      const float4 b = R.b[slot][j];
-      float y1, y2;
-      const float q = frag_q(px, pya, a, b, y1, y2);
-      const bool ha = rank < pa.end && q <= b.y;
-      if (!__any_sync(kFull, ha)) continue;
-      const float4 c = R.c[slot][j];
-      float v[9];
-      grad_fragment(pa, ha, q, y1, y2, a, b, c, v);
-      reduce_candidate<MODE>(v, ha, rank, B, nb, g2d, threshold, lane);
+      const bool two = m != 0u;
+      const int j1 = two ? __ffs(m) - 1 : j0;
+      m &= m - 1u;
+      const uint32_t rank0 = R.rank[slot][j0], rank1 = R.rank[slot][j1];
+      const float4 a0 = R.a[slot][j0], b0 = R.b[slot][j0];
+      const float4 a1 = R.a[slot][j1], b1 = R.b[slot][j1];
+      float y10, y20, y11, y21;
+      const float q0 = frag_q(px, pya, a0, b0, y10, y20);
+      const float q1 = frag_q(px, pya, a1, b1, y11, y21);
+      const bool h0 = rank0 < pa.end && q0 <= b0.y;
+      const bool h1 = two && rank1 < pa.end && q1 <= b1.y;
+      const float4 c0 = R.c[slot][j0], c1 = R.c[slot][j1];
+      const bool u0 = __any_sync(kFull, h0), u1 = __any_sync(kFull, h1);
+      float v0[9], v1[9];
+      if (u0 && u1) {
+        FragPre r0, r1;
+        frag_pre(pa, h0, q0, y10, y20, a0, b0, c0, r0);
+        frag_pre(pa, h1, q1, y11, y21, a1, b1, c1, r1);
+        frag_post(pa, r0, v0);
+        frag_post(pa, r1, v1);
+        reduce_candidate<MODE>(v0, h0, rank0, B, nb, g2d, threshold, lane);
+        reduce_candidate<MODE>(v1, h1, rank1, B, nb, g2d, threshold, lane);
+      } else if (u0) {
+        grad_fragment(pa, h0, q0, y10, y20, a0, b0, c0, v0);
+        reduce_candidate<MODE>(v0, h0, rank0, B, nb, g2d, threshold, lane);
+      } else if (u1) {
+        grad_fragment(pa, h1, q1, y11, y21, a1, b1, c1, v1);
+        reduce_candidate<MODE>(v1, h1, rank1, B, nb, g2d, threshold, lane);
+      }
     }
     __syncwarp();   // every lane is done with the slot before it is refilled
     ring_issue(R, slot, rec, ip, end, rk_next, lane);
@@ -668,44 +707,92 @@ __device__ __forceinline__ PairBwd pack_pair(const PixelBwd& a, const PixelBwd& 
   return p;
 }
 
-// One candidate of Procedure 1 at both pixels of a lane, as grad_fragment.
-// t[k] holds the two pixels' contributions to value k.
-__device__ __forceinline__ void grad_pair(PairBwd& p, bool ha, bool hb, float2 q, float y1,
-                                          float2 y2, const float4& a, const float4& b,
-                                          const float4& c, float2 t[9]) {
-  const float2 G = make_float2(ha ? ex2_approx(-q.x) : 0.0f, hb ? ex2_approx(-q.y) : 0.0f);
-  const float2 at = __fmul2_rn(f2(c.w), G);
-  const float2 alpha = make_float2(fminf(kAlphaMax, at.x), fminf(kAlphaMax, at.y));
-  const float2 oma = __ffma2_rn(alpha, f2(-1.0f), f2(1.0f));   // 1 - alpha, rounded once
-  const float2 wT = __fmul2_rn(alpha, p.T);
+// One candidate of Procedure 1 at both pixels of a lane, in the two halves of
+// frag_pre and frag_post; t[k] holds the two pixels' contributions to value k.
+struct PairPre {
+  float2 G, at, alpha, oma, inv, gc, z0, z1;
+};
+
+__device__ __forceinline__ void pair_pre(const PairBwd& p, bool ha, bool hb, float2 q, float y1,
+                                         float2 y2, const float4& a, const float4& b,
+                                         const float4& c, PairPre& r) {
+  r.G = make_float2(ha ? ex2_approx(-q.x) : 0.0f, hb ? ex2_approx(-q.y) : 0.0f);
+  r.at = __fmul2_rn(f2(c.w), r.G);
+  r.alpha = make_float2(fminf(kAlphaMax, r.at.x), fminf(kAlphaMax, r.at.y));
+  r.oma = __ffma2_rn(r.alpha, f2(-1.0f), f2(1.0f));   // 1 - alpha, rounded once
+  r.inv = make_float2(__fdividef(1.0f, r.oma.x), __fdividef(1.0f, r.oma.y));
+  r.gc = __ffma2_rn(p.g0, f2(c.x), __ffma2_rn(p.g1, f2(c.y), __fmul2_rn(p.g2, f2(c.z))));
+  // z = Sigma^-1 d (see frag_pre)
+  r.z1 = __fmul2_rn(f2(b.x), y2);
+  r.z0 = __ffma2_rn(f2(-a.w), r.z1, f2(a.z * y1));
+}
+
+__device__ __forceinline__ void pair_post(PairBwd& p, const PairPre& r, float2 t[9]) {
+  const float2 wT = __fmul2_rn(r.alpha, p.T);
   // Eq. 3
   t[5] = __fmul2_rn(p.g0, wT);
   t[6] = __fmul2_rn(p.g1, wT);
   t[7] = __fmul2_rn(p.g2, wT);
   // Eq. 7 with D_i before its update: (T g . c - D) / (1 - alpha)
-  const float2 gc = __ffma2_rn(p.g0, f2(c.x), __ffma2_rn(p.g1, f2(c.y), __fmul2_rn(p.g2, f2(c.z))));
-  const float2 dLda = __fmul2_rn(__ffma2_rn(p.T, gc, p.nD),
-                                 make_float2(__fdividef(1.0f, oma.x), __fdividef(1.0f, oma.y)));
+  const float2 dLda = __fmul2_rn(__ffma2_rn(p.T, r.gc, p.nD), r.inv);
   // Eq. 6 (dotted with g), Eq. 5
-  p.nD = __ffma2_rn(wT, gc, p.nD);
-  p.T = __fmul2_rn(p.T, oma);
+  p.nD = __ffma2_rn(wT, r.gc, p.nD);
+  p.T = __fmul2_rn(p.T, r.oma);
   // alpha = min(0.99, o G): no gradient through the clamp
-  const float2 d_at = make_float2(at.x < kAlphaMax ? dLda.x : 0.0f, at.y < kAlphaMax ? dLda.y : 0.0f);
-  t[8] = __fmul2_rn(G, d_at);
-  // z = Sigma^-1 d (see grad_fragment), weighted by dL/dpower
-  const float2 w = __fmul2_rn(at, d_at);
-  const float2 z1 = __fmul2_rn(f2(b.x), y2);
-  const float2 z0 = __ffma2_rn(f2(-a.w), z1, f2(a.z * y1));
-  t[0] = __fmul2_rn(w, z0);
-  t[1] = __fmul2_rn(w, z1);
-  t[2] = __fmul2_rn(t[0], z0);
-  t[3] = __fmul2_rn(t[0], z1);
-  t[4] = __fmul2_rn(t[1], z1);
+  const float2 d_at = make_float2(r.at.x < kAlphaMax ? dLda.x : 0.0f,
+                                  r.at.y < kAlphaMax ? dLda.y : 0.0f);
+  t[8] = __fmul2_rn(r.G, d_at);
+  // weighted by dL/dpower
+  const float2 w = __fmul2_rn(r.at, d_at);
+  t[0] = __fmul2_rn(w, r.z0);
+  t[1] = __fmul2_rn(w, r.z1);
+  t[2] = __fmul2_rn(t[0], r.z0);
+  t[3] = __fmul2_rn(t[0], r.z1);
+  t[4] = __fmul2_rn(t[1], r.z1);
 }
 
-// The 8x8 quadrant (two pixels per lane) with the pixel pair packed; in
-// GS_REDUCE_FRAGMENT mode each pixel's fragment adds its own values to the
-// splat's accumulators.
+// The values of a lane: its two pixels' contributions added.
+__device__ __forceinline__ void pair_post_sum(PairBwd& p, const PairPre& r, float v[9]) {
+  float2 t[9];
+  pair_post(p, r, t);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = t[k].x + t[k].y;
+}
+
+// GS_REDUCE_FRAGMENT: each pixel's fragment adds its own values to the
+// splat's accumulators (the per-fragment atomics of the ablation).
+__device__ __forceinline__ void pair_fragment_atomics(PairBwd& p, const PairPre& r, bool ha,
+                                                      bool hb, uint32_t rank, float* g2d) {
+  float2 t[9];
+  pair_post(p, r, t);
+  float va9[9], vb9[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    va9[k] = t[k].x;
+    vb9[k] = t[k].y;
+  }
+  if (ha) red_add9(g2d + (size_t)rank * 12, va9);
+  if (hb) red_add9(g2d + (size_t)rank * 12, vb9);
+}
+
+// One candidate at both pixels, to the reduction of the mode.
+template <int MODE>
+__device__ __forceinline__ void pair_one(PairBwd& p, bool ha, bool hb, float2 q, float y1,
+                                         float2 y2, const float4& a, const float4& b,
+                                         const float4& c, uint32_t rank, GradBatch& B, int& nb,
+                                         float* g2d, int threshold, int lane) {
+  PairPre r;
+  pair_pre(p, ha, hb, q, y1, y2, a, b, c, r);
+  if (MODE == GS_REDUCE_FRAGMENT) {
+    pair_fragment_atomics(p, r, ha, hb, rank, g2d);
+  } else {
+    float v[9];
+    pair_post_sum(p, r, v);
+    reduce_candidate<MODE>(v, ha || hb, rank, B, nb, g2d, threshold, lane);
+  }
+}
+
+// The 8x8 quadrant (two pixels per lane) with the pixel pair packed.
 template <int MODE>
 __device__ __forceinline__ void bwd_item_pair(BwdRing& R, GradBatch& B,
                                               const SplatRec* __restrict__ rec,
@@ -746,35 +833,44 @@ __device__ __forceinline__ void bwd_item_pair(BwdRing& R, GradBatch& B,
     uint32_t m = __ballot_sync(kFull, (uint32_t)lane < cnt &&
                                           rect_may_hit(R.a[slot][lane], R.b[slot][lane], xs, ys,
                                                        7.f, 7.f));
+    // Two candidates per step, as in bwd_item.
     while (m) {
-      const int j = __ffs(m) - 1;
+      const int j0 = __ffs(m) - 1;
       m &= m - 1u;
-      const uint32_t rank = R.rank[slot][j];
-      const float4 a = R.a[slot][j];
-      const float4 b = R.b[slot][j];
-      float y1;
-      float2 y2;
-      const float2 q = frag_q_pair(px, py, a, b, y1, y2);
-      const bool ha = rank < pp.end_a && q.x <= b.y;
-      const bool hb = rank < pp.end_b && q.y <= b.y;
-      const float4 c = R.c[slot][j];
-      if (!__any_sync(kFull, ha || hb)) continue;
-      float2 t[9];
-      grad_pair(pp, ha, hb, q, y1, y2, a, b, c, t);
-      if (MODE == GS_REDUCE_FRAGMENT) {
-        float va9[9], vb9[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          va9[k] = t[k].x;
-          vb9[k] = t[k].y;
+      const bool two = m != 0u;
+      const int j1 = two ? __ffs(m) - 1 : j0;
+      m &= m - 1u;
+      const uint32_t rank0 = R.rank[slot][j0], rank1 = R.rank[slot][j1];
+      const float4 a0 = R.a[slot][j0], b0 = R.b[slot][j0];
+      const float4 a1 = R.a[slot][j1], b1 = R.b[slot][j1];
+      float y10, y11;
+      float2 y20, y21;
+      const float2 q0 = frag_q_pair(px, py, a0, b0, y10, y20);
+      const float2 q1 = frag_q_pair(px, py, a1, b1, y11, y21);
+      const bool ha0 = rank0 < pp.end_a && q0.x <= b0.y;
+      const bool hb0 = rank0 < pp.end_b && q0.y <= b0.y;
+      const bool ha1 = two && rank1 < pp.end_a && q1.x <= b1.y;
+      const bool hb1 = two && rank1 < pp.end_b && q1.y <= b1.y;
+      const float4 c0 = R.c[slot][j0], c1 = R.c[slot][j1];
+      const bool u0 = __any_sync(kFull, ha0 || hb0), u1 = __any_sync(kFull, ha1 || hb1);
+      if (u0 && u1) {
+        PairPre r0, r1;
+        pair_pre(pp, ha0, hb0, q0, y10, y20, a0, b0, c0, r0);
+        pair_pre(pp, ha1, hb1, q1, y11, y21, a1, b1, c1, r1);
+        if (MODE == GS_REDUCE_FRAGMENT) {
+          pair_fragment_atomics(pp, r0, ha0, hb0, rank0, g2d);
+          pair_fragment_atomics(pp, r1, ha1, hb1, rank1, g2d);
+        } else {
+          float v0[9], v1[9];
+          pair_post_sum(pp, r0, v0);
+          pair_post_sum(pp, r1, v1);
+          reduce_candidate<MODE>(v0, ha0 || hb0, rank0, B, nb, g2d, threshold, lane);
+          reduce_candidate<MODE>(v1, ha1 || hb1, rank1, B, nb, g2d, threshold, lane);
         }
-        if (ha) red_add9(g2d + (size_t)rank * 12, va9);
-        if (hb) red_add9(g2d + (size_t)rank * 12, vb9);
-      } else {
-        float v[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) v[k] = t[k].x + t[k].y;
-        reduce_candidate<MODE>(v, ha || hb, rank, B, nb, g2d, threshold, lane);
+      } else if (u0) {
+        pair_one<MODE>(pp, ha0, hb0, q0, y10, y20, a0, b0, c0, rank0, B, nb, g2d, threshold, lane);
+      } else if (u1) {
+        pair_one<MODE>(pp, ha1, hb1, q1, y11, y21, a1, b1, c1, rank1, B, nb, g2d, threshold, lane);
       }
     }
     __syncwarp();   // every lane is done with the slot before it is refilled
