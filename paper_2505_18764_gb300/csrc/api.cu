@@ -37,6 +37,7 @@ int noalloc_stalled_pass(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,
                          uint32_t, cudaStream_t);
 cudaError_t launch_digit_hist(const uint32_t*, uint32_t, int, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bump_epoch(uint32_t*, cudaStream_t);
+cudaError_t launch_sort_begin(uint32_t*, uint32_t*, int, cudaStream_t);
 cudaError_t launch_bin_count(const uint32_t*, const SplatRec*, const uint2*, SplatRec*, float*,
                              Header*, unsigned long long*, const uint32_t*, uint32_t*, uint2*,
                              uint32_t, int, int, int, cudaStream_t, uint32_t*, uint32_t);
@@ -324,8 +325,7 @@ int gs_sort(gs_workspace* ws, gs_stream_t stream) {
   unsigned long long* status = at<unsigned long long>(ws, L_STATUS);
   const int grid_cap = num_sms() * kPersistentPerSm;
   // a sort may repeat without a new projection: fresh tile counters and look-back tags
-  GS_CUDA(cudaMemsetAsync(&hdr->tile_counter[0], 0, 4 * sizeof(uint32_t), st), "sort counters");
-  GS_CUDA(launch_bump_epoch(epoch, st), "epoch kernel");
+  GS_CUDA(launch_sort_begin(epoch, &hdr->tile_counter[0], 4, st), "sort setup kernel");
   uint32_t* bufs_k[2] = {at<uint32_t>(ws, L_KA), at<uint32_t>(ws, L_KB)};
   uint32_t* bufs_v[2] = {at<uint32_t>(ws, L_VA), at<uint32_t>(ws, L_VB)};
   for (int pass = 0; pass < 4; ++pass) {
@@ -617,8 +617,9 @@ int project_backward_impl(gs_workspace* ws, const float* means, const float* sca
                              at<Header>(ws, L_HDR), d_means, d_scales, d_quats, d_opacities, d_sh,
                              num_sms(), st, store_grads, live_list(ws), ls),
           "projection backward kernel");
-  // store: the list now holds every row this view wrote; add: it no longer covers them
-  GS_CUDA(launch_set_word(ls + 1, store_grads ? 1u : 0u, st), "list state");
+  // store: the list now holds every row this view wrote (an adding backward
+  // marks it invalid itself)
+  if (store_grads) GS_CUDA(launch_set_word(ls + 1, 1u, st), "list state");
   return GS_OK;
 }
 }  // namespace

@@ -675,6 +675,8 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) project_bwd_kernel(
   // STORE with a valid list: every non-zero row was on it and has been zeroed
   // (zero_listed_kernel), so the rows without a gradient need nothing
   const bool zero_nonlive = STORE && list_state[1] == 0u;
+  // adding: the list no longer covers every non-zero row (nothing here reads it)
+  if (!STORE && blockIdx.x == 0 && threadIdx.x == 0) list_state[1] = 0u;
   __shared__ __align__(16) float s_rows[kProjBwdWarps][32 * P];
   __shared__ uint32_t s_queue[kProjBwdWarps][64];
   const int lane = threadIdx.x & 31;

@@ -223,6 +223,11 @@ __global__ void __launch_bounds__(256) digit_hist_kernel(const uint32_t* __restr
 }
 
 __global__ void bump_epoch_kernel(uint32_t* epoch) { *epoch += 1u; }
+// A new epoch and n zeroed tile counters: the start of a sort.
+__global__ void sort_begin_kernel(uint32_t* epoch, uint32_t* counters, int n) {
+  if (threadIdx.x == 0) *epoch += 1u;
+  if ((int)threadIdx.x < n) counters[threadIdx.x] = 0u;
+}
 __global__ void set_word_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
 cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in,
@@ -260,6 +265,11 @@ cudaError_t launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, uint
 
 cudaError_t launch_bump_epoch(uint32_t* epoch, cudaStream_t st) {
   bump_epoch_kernel<<<1, 1, 0, st>>>(epoch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_begin(uint32_t* epoch, uint32_t* counters, int n, cudaStream_t st) {
+  sort_begin_kernel<<<1, 32, 0, st>>>(epoch, counters, n);
   return cudaGetLastError();
 }
 
