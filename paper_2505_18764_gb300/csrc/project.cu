@@ -217,14 +217,33 @@ __device__ __forceinline__ uint32_t project_splat(
   constexpr int K = (DEG + 1) * (DEG + 1);
   float Y[16];
   sh_eval(DEG, vx, vy, vz, Y);
-  ShRow<DEG> row;
-  row.load(sh + (size_t)i * K * 3, sh_vec);
   float col[3] = {0.5f, 0.5f, 0.5f};
+  if (K == 16 && sh_vec) {
+    // degree 3: the 48 coefficients in three rounds of four float4 loads, the
+    // rounds kept apart so that at most 16 are live (the kernel then fits four
+    // CTAs per SM); each channel still adds its terms in coefficient order
+    const float4* q = reinterpret_cast<const float4*>(sh + (size_t)i * K * 3);
 #pragma unroll
-  for (int kk = 0; kk < K; ++kk) {
-    col[0] += row.v[kk * 3 + 0] * Y[kk];
-    col[1] += row.v[kk * 3 + 1] * Y[kk];
-    col[2] += row.v[kk * 3 + 2] * Y[kk];
+    for (int ch = 0; ch < 3; ++ch) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 t = q[4 * ch + u];
+        v[4 * u] = t.x; v[4 * u + 1] = t.y; v[4 * u + 2] = t.z; v[4 * u + 3] = t.w;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) col[(16 * ch + e) % 3] += v[e] * Y[(16 * ch + e) / 3];
+      asm volatile("" ::: "memory");
+    }
+  } else {
+    ShRow<DEG> row;
+    row.load(sh + (size_t)i * K * 3, sh_vec);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+      col[0] += row.v[kk * 3 + 0] * Y[kk];
+      col[1] += row.v[kk * 3 + 1] * Y[kk];
+      col[2] += row.v[kk * 3 + 2] * Y[kk];
+    }
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -243,7 +262,7 @@ __device__ __forceinline__ uint32_t project_splat(
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kProjThreads, 2) project_fwd_kernel(
+__global__ void __launch_bounds__(kProjThreads, 4) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float4* __restrict__ quats, const float* __restrict__ opac,
     const float* __restrict__ sh, int n, CamDev cam, int clamp01, int sh_vec,
@@ -863,7 +882,7 @@ cudaError_t launch_project_fwd(const float* means, const float* scales, const fl
                                uint32_t* keys, Header* hdr, uint2* ranges, int n_ranges,
                                uint32_t* epoch, int num_sms, cudaStream_t st) {
   int blocks = (n + kProjThreads - 1) / kProjThreads;
-  const int cap = num_sms * 2;  // persistent: one wave, two CTAs per SM (the launch bound)
+  const int cap = num_sms * 4;  // persistent: one wave, four CTAs per SM (the launch bound)
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   const float4* q4 = reinterpret_cast<const float4*>(quats);
