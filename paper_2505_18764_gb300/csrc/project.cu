@@ -628,10 +628,14 @@ __device__ __forceinline__ void project_bwd_batch(
   }
   gather_rows<3, P>(rows, 0, means, id, count, lane);
   gather_rows<3, P>(rows, 3, scales, id, count, lane);
-  if (Row::kVec && sh_vec)
-    gather_rows4<Row::kSh / 4, P>(rows, Row::kShOff, sh, id, count, lane);
-  else
+  if constexpr (Row::kVec) {   // float4 copies only where a row is whole 16-byte words
+    if (sh_vec)
+      gather_rows4<Row::kSh / 4, P>(rows, Row::kShOff, sh, id, count, lane);
+    else
+      gather_rows<Row::kSh, P>(rows, Row::kShOff, sh, id, count, lane);
+  } else {
     gather_rows<Row::kSh, P>(rows, Row::kShOff, sh, id, count, lane);
+  }
   __syncwarp();
   if (mine) {
     const float4 gq = project_bwd_splat<DEG>(rows + lane * P, quat, ga, gb, cam, clamp01);
@@ -666,10 +670,14 @@ __device__ __forceinline__ void project_bwd_batch(
   asm volatile("" ::: "memory");
   scatter_add_rows<3, P, STORE>(rows, 0, d_means, id, count, lane);
   scatter_add_rows<3, P, STORE>(rows, 3, d_scales, id, count, lane);
-  if (Row::kVec && sh_vec)
-    scatter_add_rows4<Row::kSh / 4, P, STORE>(rows, Row::kShOff, d_sh, id, count, lane);
-  else
+  if constexpr (Row::kVec) {
+    if (sh_vec)
+      scatter_add_rows4<Row::kSh / 4, P, STORE>(rows, Row::kShOff, d_sh, id, count, lane);
+    else
+      scatter_add_rows<Row::kSh, P, STORE>(rows, Row::kShOff, d_sh, id, count, lane);
+  } else {
     scatter_add_rows<Row::kSh, P, STORE>(rows, Row::kShOff, d_sh, id, count, lane);
+  }
   __syncwarp();   // the rows are reused by the next batch
 }
 
