@@ -33,9 +33,11 @@
 // dL/dc = g alpha T (Eq. 3), dL/dalpha = g . (c T - C') / (1 - alpha) (Eq. 7),
 // then C' -= T alpha c (Eq. 6) and T *= 1 - alpha (Eq. 5).  The chain rule to
 // the 2D splat parameters follows; the nine per-fragment values of a lane's
-// pixels are added, reduced over the warp by a transpose-reduce, and one
-// vector-atomic triple per (splat, footprint) reaches global memory
-// (Procedure 2's role).
+// pixels are added, summed over the warp through shared memory in batches of
+// four candidates, and one vector-atomic triple per (splat, footprint) reaches
+// global memory (Procedure 2's role).  Both passes take their candidates two
+// per step, evaluating what does not depend on the pixel's running state for
+// both before the depth-ordered updates.
 #include "common.cuh"
 
 namespace gsr {
