@@ -266,8 +266,9 @@ def run_ours(args, rank, world, local_rank):
     P_live = cnt["live_pairs"]
     npix = H * W
     passes = ws.c.pair_passes
-    # sort: epoch + 4 passes; bin: count, chunk setup, emit, pair-sort passes, ranges, item
-    # order; blend_bwd: item reorder + raster
+    # project; sort: setup (epoch, tile counters) + 4 passes; bin: count, chunk setup, emit,
+    # pair-sort passes, ranges, item order; blend_fwd; loss; blend_bwd: item reorder +
+    # raster; project_bwd
     kernels_per_step = 1 + 5 + (3 + passes + 2) + 1 + 1 + 2 + 1
     K_sh = 16
 
